@@ -1,0 +1,191 @@
+/*
+ * beta_splat.h -- C ABI of the GB300 (sm_103a) Beta-splatting rasterizer.
+ *
+ * Deformable Beta Splatting (arXiv 2501.18630): 3D ellipsoidal Beta
+ * primitives {mu, o, q, s, b, f} (Sec. 3.2) are projected with EWA
+ * (Sigma' = J W Sigma W^T J^T), binned into 16x16 pixel tiles, depth-sorted,
+ * and composited front to back with the Beta kernel
+ *     alpha = min(alpha_max, o (1 - r^2)^beta),  beta = 4 e^b    (Eq. 2, Eq. eq:beta)
+ *     C(x) = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j)              (Eq. C)
+ * with view-dependent spherical-Beta colour                          (Sec. 3.3)
+ *     c(V) = c0 + sum_m max(R_m . V, 0)^(4 e^{b_m}) c_m.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Memory: the caller owns every buffer.  The library never allocates or
+ *    frees device memory; sizes come from the *_bytes() queries.  Pointers
+ *    are DEVICE pointers unless the argument is documented as host.
+ *  - Streams: every compute call is asynchronous on `stream` (a
+ *    cudaStream_t; NULL means the legacy default stream), never
+ *    synchronises, and issues only kernel launches.
+ *  - Errors: host-detectable argument errors (null pointers, bad sizes,
+ *    unsupported options, too small workspace) are returned immediately as
+ *    a negative beta_status and nothing is launched.  A failed launch
+ *    returns BETA_ERR_CUDA.  Data-dependent errors (pair capacity overflow,
+ *    a bounded spin-wait that ran out) are written to the device status word
+ *    `d_status` (int32), which the caller reads after synchronising; every
+ *    kernel downstream of a non-zero status skips its work.
+ *  - Culling: non-finite primitives, centres with camera depth <= near and
+ *    primitives whose support misses the image touch no tile.  They are not
+ *    errors.
+ *
+ * Primitive parameters: one float32 plane per scalar, planes of `pitch`
+ * floats (pitch >= n, multiple of 4), plane index
+ *     0-2 mean xyz | 3-5 log-scale | 6-9 quaternion wxyz (unnormalised) |
+ *     10 opacity logit | 11 shape b | 12-14 base colour c0 |
+ *     15+6m+{0..5}: lobe m theta, phi, b_m, c_m rgb          (3+6M features)
+ * i.e. 15 + 6M planes.  s = exp(log-scale), o = sigmoid(logit),
+ * R_m = (sin theta cos phi, sin theta sin phi, cos theta).
+ *
+ * Batches of views: V <= BETA_MAX_VIEWS cameras.  View v has
+ * ntx_v x nty_v tiles, ntx_v = ceil(W_v / tile_w); global tile ids run view
+ * by view (row-major inside a view).  Pixel outputs of view v start at
+ * pixel offset P_v = sum_{u<v} W_u H_u: colour is planar per view,
+ * color[3 P_v + ch W_v H_v + y W_v + x]; T_final and n_contrib are
+ * [P_v + y W_v + x].  A record is (view, primitive) = v * pitch + i.
+ */
+#ifndef BETA_SPLAT_H
+#define BETA_SPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* beta_stream_t; /* == cudaStream_t */
+
+typedef enum {
+  BETA_OK = 0,
+  BETA_ERR_ARG = -1,         /* invalid argument (host-detected)                  */
+  BETA_ERR_CAPACITY = -2,    /* more (tile, primitive) pairs than pair_capacity   */
+  BETA_ERR_CUDA = -3,        /* a kernel launch failed                            */
+  BETA_ERR_TIMEOUT = -4,     /* a bounded device spin-wait gave up                */
+  BETA_ERR_UNSUPPORTED = -5, /* option outside the supported set                  */
+  BETA_ERR_WORKSPACE = -6    /* workspace smaller than the *_bytes() query        */
+} beta_status;
+
+#define BETA_MAX_LOBES 8
+#define BETA_MAX_VIEWS 64
+
+/* Primitive parameters (host struct; `planes` is a device pointer). */
+typedef struct {
+  int32_t n;          /* number of primitives, >= 0                           */
+  int32_t pitch;      /* floats per plane, >= n, multiple of 4                */
+  int32_t n_lobes;    /* spherical-Beta lobes M, 0..BETA_MAX_LOBES            */
+  int32_t reserved;   /* must be 0                                            */
+  const float* planes;/* device, (15 + 6M) x pitch float32, layout above     */
+} beta_params;
+
+/* Pinhole camera (host struct).  World point X maps to camera space as
+ * R X + t (OpenCV axes: x right, y down, z forward); pixel (i, j) is
+ * sampled at its centre (i + 1/2, j + 1/2). */
+typedef struct {
+  float R[9];          /* row-major world->camera rotation                    */
+  float t[3];
+  float fx, fy, cx, cy;
+  float near_plane;    /* centres with camera z <= near_plane are culled      */
+  int32_t width, height;
+  float bg[3];         /* background, weighted by the final transmittance     */
+} beta_camera;
+
+/* Render options (host struct).  beta_default_opts() fills the defaults. */
+typedef struct {
+  int32_t tile_w, tile_h; /* pixel tile; 16 x 16 is the supported shape      */
+  int32_t batch_s;        /* records staged per raster batch: 64, 128 or 256 */
+  int32_t color_mode;     /* 0: c0 + lobes, 1: c0 only (diffuse), 2: lobes only (specular) */
+  float t_eps;            /* stop before a primitive once T < t_eps (2^-19)   */
+  float alpha_max;        /* alpha = min(alpha_max, o B)   (0.99)             */
+  float blur_eps;         /* added to the diagonal of Sigma' (0)              */
+  float b_lo, b_hi;       /* render only primitives with b_lo <= b < b_hi (geometry
+                             decomposition, Sec. 4.3); -inf / +inf by default */
+} beta_opts;
+
+void beta_default_opts(beta_opts* opt /* host */);
+const char* beta_status_string(int code);
+int32_t beta_version(void);
+
+/* ---- sizes (host-only queries, no device work) ------------------------ */
+
+/* Bytes of the projection buffer `proj` for V views: 76 bytes per record
+ * (64-byte raster record, 8-byte tile rectangle, 4-byte depth key). */
+size_t beta_proj_bytes(int32_t pitch, int32_t n_views);
+/* Total tiles of a batch of views (the length of tile_ranges is this + 1). */
+int64_t beta_total_tiles(const beta_camera* cams /* host */, int32_t n_views, const beta_opts* opt);
+/* Total pixels of a batch of views. */
+int64_t beta_total_pixels(const beta_camera* cams /* host */, int32_t n_views);
+/* Workspace of beta_bin_sort for a pair capacity (radix-sort buffers,
+ * look-back tables, scan sums). */
+size_t beta_binsort_workspace_bytes(int32_t pitch, int32_t n_views, int64_t pair_capacity,
+                                    const beta_camera* cams /* host */, const beta_opts* opt);
+/* Workspace of beta_raster_bwd: per-record 2D gradients, 10 floats each. */
+size_t beta_grad2d_bytes(int32_t pitch, int32_t n_views);
+/* Workspace of beta_l1_loss (per-block partial sums). */
+size_t beta_l1_workspace_bytes(const beta_camera* cams /* host */, int32_t n_views);
+
+/* ---- the hot path ----------------------------------------------------- */
+
+/* Step 1 (Sec. 3.2, Sec. 3.3): per (view, primitive) activations, EWA
+ * projection Sigma' = J W R S S^T R^T W^T J^T, projected centre, Beta shape
+ * beta = 4 e^b, spherical-Beta colour, tile rectangle and depth key.
+ * Writes `proj` (beta_proj_bytes(pitch, n_views) bytes, 16-byte aligned). */
+int beta_project(const beta_params* prm /* host */, const beta_camera* cams /* host [n_views] */,
+                 int32_t n_views, const beta_opts* opt /* host */, void* proj,
+                 beta_stream_t stream);
+
+/* Step 2 (Sec. 3.2: "sorting overlapping primitives by depth"): emits one
+ * (tile, record) pair per tile each record's rectangle touches, sorts the
+ * pairs by (global tile, depth key, primitive index) with a project-written
+ * onesweep LSD radix sort, and writes the per-tile ranges.
+ *   pair_vals   [pair_capacity] out: record of every sorted pair
+ *   tile_ranges [total_tiles + 1] out: pairs of tile g are
+ *               pair_vals[tile_ranges[g] .. tile_ranges[g + 1])
+ *   d_pair_count (int64) out: number of pairs K (also when K > capacity)
+ *   d_status    out: reset to BETA_OK, then BETA_ERR_CAPACITY if
+ *               K > pair_capacity or BETA_ERR_TIMEOUT if a spin gave up.
+ *   ws, ws_bytes: workspace of beta_binsort_workspace_bytes(). */
+int beta_bin_sort(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                  const beta_opts* opt, const void* proj, uint32_t* pair_vals,
+                  int64_t pair_capacity, uint32_t* tile_ranges, int64_t* d_pair_count,
+                  int32_t* d_status, void* ws, size_t ws_bytes, beta_stream_t stream);
+
+/* Step 3 (Eq. C): front-to-back compositing of every tile's sorted list.
+ *   color     [3 x total_pixels] out: C + T_final * bg (planar per view)
+ *   T_final   [total_pixels] out: final transmittance
+ *   n_contrib [total_pixels] out: 1 + position (inside the tile's list) of
+ *             the last primitive that contributed, 0 if none.
+ *   d_status  in: if non-zero the kernel writes nothing. */
+int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                    const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
+                    const uint32_t* tile_ranges, float* color, float* T_final,
+                    uint32_t* n_contrib, const int32_t* d_status, beta_stream_t stream);
+
+/* Per-pixel L1 loss of a batch of views (Sec. 3.4, the L1 term):
+ *   loss[v] = mean over 3 W_v H_v of |color - target|   (device float[n_views], out)
+ *   dL_dcolor = sign(color - target) / (3 W_v H_v)       (same layout as color, out)
+ * so the gradient is that of sum_v loss[v].  ws: beta_l1_workspace_bytes(). */
+int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color,
+                 const float* target, float* loss, float* dL_dcolor, void* ws, size_t ws_bytes,
+                 beta_stream_t stream);
+
+/* Step 4: reverse-order backward of Eq. C through the projection to the raw
+ * parameters.  Walks each pixel's list from its last contributor down,
+ * recovering T by division, accumulates per-record 2D gradients
+ * (d mu', d Sigma', d o, d beta, d colour) with warp-reduced atomics into
+ * grad2d, then chains them through Sec. 3.2/3.3 to every raw parameter and
+ * sums over views.
+ *   dL_dcolor  [3 x total_pixels] in
+ *   grad2d     workspace of beta_grad2d_bytes() (overwritten)
+ *   grad_planes out: (15 + 6M) x pitch float32, same layout as the params,
+ *              overwritten for i < n (padding lanes are left untouched). */
+int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                    const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
+                    const uint32_t* tile_ranges, const float* T_final,
+                    const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
+                    float* grad_planes, const int32_t* d_status, beta_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BETA_SPLAT_H */

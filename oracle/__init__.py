@@ -211,23 +211,24 @@ def bin_pairs(planes, n, n_lobes, cams, blur_eps=0.0, tile_w=16, tile_h=16, pitc
         rects, keys, binned = rule_rects(planes, n, n_lobes, cam, blur_eps, tile_w, tile_h)
         ntx, nty = n_tiles(cam, tile_w, tile_h)
         idx = np.nonzero(binned)[0]
-        for i in idx:
-            tx0, tx1, ty0, ty1 = rects[i]
-            ty, tx = np.meshgrid(np.arange(ty0, ty1 + 1), np.arange(tx0, tx1 + 1), indexing="ij")
-            g = tile_off + (ty * ntx + tx).reshape(-1)
-            all_tiles.append(g.astype(np.int64))
-            all_keys.append(np.full(g.shape, keys[i], np.int64))
-            all_rec.append(np.full(g.shape, v * pitch + i, np.int64))
+        r = rects[idx].astype(np.int64)
+        wx = r[:, 1] - r[:, 0] + 1
+        cnt = wx * (r[:, 3] - r[:, 2] + 1)
+        prim = np.repeat(idx, cnt)
+        first = np.repeat(np.cumsum(cnt) - cnt, cnt)
+        local = np.arange(cnt.sum(), dtype=np.int64) - first
+        rw = np.repeat(np.arange(len(idx)), cnt)
+        ty = r[rw, 2] + local // wx[rw]
+        tx = r[rw, 0] + local % wx[rw]
+        all_tiles.append(tile_off + ty * ntx + tx)
+        all_keys.append(keys[prim].astype(np.int64))
+        all_rec.append(v * pitch + prim.astype(np.int64))
         tile_off += ntx * nty
-    if all_tiles:
-        tiles = np.concatenate(all_tiles)
-        keys = np.concatenate(all_keys)
-        recs = np.concatenate(all_rec)
-        order = np.lexsort((recs, keys, tiles))
-        tiles, recs = tiles[order], recs[order]
-    else:
-        tiles = np.zeros(0, np.int64)
-        recs = np.zeros(0, np.int64)
+    tiles = np.concatenate(all_tiles) if all_tiles else np.zeros(0, np.int64)
+    keys = np.concatenate(all_keys) if all_keys else np.zeros(0, np.int64)
+    recs = np.concatenate(all_rec) if all_rec else np.zeros(0, np.int64)
+    order = np.lexsort((recs, keys, tiles))
+    tiles, recs = tiles[order], recs[order]
     ranges = np.searchsorted(tiles, np.arange(tile_off + 1), side="left").astype(np.uint32)
     return tiles.astype(np.uint32), recs.astype(np.uint32), ranges
 

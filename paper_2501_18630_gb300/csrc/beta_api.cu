@@ -1,0 +1,253 @@
+// beta_api.cu -- the C ABI declared in include/beta_splat.h: argument
+// validation, view tables, workspace carving and kernel launches.  Every
+// entry point only enqueues kernels on the caller's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "beta_internal.cuh"
+#include "beta_splat.h"
+
+using namespace beta;
+
+namespace {
+
+constexpr int32_t kVersion = 1;
+
+bool valid_params(const beta_params* p) {
+  if (!p) return false;
+  if (p->n < 0 || p->pitch < p->n || p->pitch % 4 != 0 || p->pitch <= 0) return false;
+  if (p->n_lobes < 0 || p->n_lobes > BETA_MAX_LOBES || p->reserved != 0) return false;
+  if (p->n > 0 && !p->planes) return false;
+  if (((uintptr_t)p->planes & 15u) != 0) return false;
+  return true;
+}
+
+int check_opts(const beta_opts* o) {
+  if (!o) return BETA_ERR_ARG;
+  if (o->tile_w != 16 || o->tile_h != 16) return BETA_ERR_UNSUPPORTED;
+  if (o->batch_s != 64 && o->batch_s != 128 && o->batch_s != 256) return BETA_ERR_UNSUPPORTED;
+  if (o->color_mode < 0 || o->color_mode > 2) return BETA_ERR_ARG;
+  if (!(o->t_eps >= 0.0f && o->t_eps < 1.0f)) return BETA_ERR_ARG;
+  if (!(o->alpha_max > 0.0f && o->alpha_max < 1.0f)) return BETA_ERR_ARG;
+  if (!(o->blur_eps >= 0.0f) || !isfinite(o->blur_eps)) return BETA_ERR_ARG;
+  if (isnan(o->b_lo) || isnan(o->b_hi)) return BETA_ERR_ARG;
+  return BETA_OK;
+}
+
+int build_views(const beta_camera* cams, int32_t n_views, const beta_opts* opt, ViewTable& vt) {
+  if (!cams || n_views <= 0 || n_views > BETA_MAX_VIEWS) return BETA_ERR_ARG;
+  memset(&vt, 0, sizeof(vt));
+  vt.n_views = n_views;
+  int64_t tiles = 0, pix = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const beta_camera& c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || c.width > 65535 * 16 || c.height > 65535 * 16) return BETA_ERR_ARG;
+    for (int k = 0; k < 9; ++k)
+      if (!isfinite(c.R[k])) return BETA_ERR_ARG;
+    for (int k = 0; k < 3; ++k)
+      if (!isfinite(c.t[k]) || !isfinite(c.bg[k])) return BETA_ERR_ARG;
+    if (!isfinite(c.fx) || !isfinite(c.fy) || !isfinite(c.cx) || !isfinite(c.cy) || !(c.near_plane > 0.0f))
+      return BETA_ERR_ARG;
+    ViewDev& d = vt.v[v];
+    memcpy(d.R, c.R, sizeof(d.R));
+    memcpy(d.t, c.t, sizeof(d.t));
+    d.fx = c.fx;
+    d.fy = c.fy;
+    d.cx = c.cx;
+    d.cy = c.cy;
+    d.near_plane = c.near_plane;
+    // camera position -R^T t (fp64, rounded once)
+    for (int r = 0; r < 3; ++r)
+      d.campos[r] = (float)-((double)c.R[0 * 3 + r] * c.t[0] + (double)c.R[1 * 3 + r] * c.t[1] +
+                              (double)c.R[2 * 3 + r] * c.t[2]);
+    memcpy(d.bg, c.bg, sizeof(d.bg));
+    d.width = c.width;
+    d.height = c.height;
+    d.ntx = (c.width + opt->tile_w - 1) / opt->tile_w;
+    d.nty = (c.height + opt->tile_h - 1) / opt->tile_h;
+    d.tile_off = (int32_t)tiles;
+    d.pix_off = pix;
+    tiles += (int64_t)d.ntx * d.nty;
+    pix += (int64_t)c.width * c.height;
+  }
+  if (tiles >= (1ll << 30)) return BETA_ERR_ARG;
+  vt.total_tiles = (int32_t)tiles;
+  vt.total_pixels = pix;
+  return BETA_OK;
+}
+
+RenderOpts render_opts(const beta_opts* o) {
+  RenderOpts r;
+  r.t_eps = o->t_eps;
+  r.alpha_max = o->alpha_max;
+  r.blur_eps = o->blur_eps;
+  r.b_lo = o->b_lo;
+  r.b_hi = o->b_hi;
+  r.color_mode = o->color_mode;
+  return r;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? BETA_OK : BETA_ERR_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+void beta_default_opts(beta_opts* o) {
+  if (!o) return;
+  o->tile_w = 16;
+  o->tile_h = 16;
+  o->batch_s = 256;
+  o->color_mode = 0;
+  o->t_eps = 1.9073486328125e-06f;  // 2^-19
+  o->alpha_max = 0.99f;
+  o->blur_eps = 0.0f;
+  o->b_lo = -INFINITY;
+  o->b_hi = INFINITY;
+}
+
+const char* beta_status_string(int code) {
+  switch (code) {
+    case BETA_OK: return "ok";
+    case BETA_ERR_ARG: return "invalid argument";
+    case BETA_ERR_CAPACITY: return "pair capacity exceeded";
+    case BETA_ERR_CUDA: return "CUDA launch failed";
+    case BETA_ERR_TIMEOUT: return "device spin-wait timed out";
+    case BETA_ERR_UNSUPPORTED: return "unsupported option";
+    case BETA_ERR_WORKSPACE: return "workspace too small";
+    default: return "unknown status";
+  }
+}
+
+int32_t beta_version(void) { return kVersion; }
+
+size_t beta_proj_bytes(int32_t pitch, int32_t n_views) {
+  if (pitch <= 0 || n_views <= 0) return 0;
+  return (size_t)pitch * n_views * 76;
+}
+
+int64_t beta_total_tiles(const beta_camera* cams, int32_t n_views, const beta_opts* opt) {
+  ViewTable vt;
+  if (check_opts(opt) != BETA_OK || build_views(cams, n_views, opt, vt) != BETA_OK) return -1;
+  return vt.total_tiles;
+}
+
+int64_t beta_total_pixels(const beta_camera* cams, int32_t n_views) {
+  beta_opts o;
+  beta_default_opts(&o);
+  ViewTable vt;
+  if (build_views(cams, n_views, &o, vt) != BETA_OK) return -1;
+  return vt.total_pixels;
+}
+
+size_t beta_binsort_workspace_bytes(int32_t pitch, int32_t n_views, int64_t cap,
+                                    const beta_camera* cams, const beta_opts* opt) {
+  ViewTable vt;
+  if (pitch <= 0 || cap < 0 || check_opts(opt) != BETA_OK || build_views(cams, n_views, opt, vt) != BETA_OK)
+    return 0;
+  return binsort_ws_bytes((int64_t)pitch * n_views, cap, vt.total_tiles);
+}
+
+size_t beta_grad2d_bytes(int32_t pitch, int32_t n_views) {
+  if (pitch <= 0 || n_views <= 0) return 0;
+  return (size_t)pitch * n_views * kGrad2d * sizeof(float);
+}
+
+size_t beta_l1_workspace_bytes(const beta_camera* cams, int32_t n_views) {
+  beta_opts o;
+  beta_default_opts(&o);
+  ViewTable vt;
+  if (build_views(cams, n_views, &o, vt) != BETA_OK) return 0;
+  return l1_ws_bytes(vt);
+}
+
+int beta_project(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                 const beta_opts* opt, void* proj, beta_stream_t stream) {
+  if (!valid_params(prm) || !proj || !aligned16(proj)) return BETA_ERR_ARG;
+  int e = check_opts(opt);
+  if (e != BETA_OK) return e;
+  ViewTable vt;
+  if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  if ((int64_t)prm->pitch * n_views >= (1ll << 32)) return BETA_ERR_ARG;
+  ProjBuffers pb = proj_layout(proj, prm->pitch, n_views);
+  return cuda_status(launch_project(prm->planes, prm->n, prm->pitch, prm->n_lobes, vt,
+                                    render_opts(opt), pb, (cudaStream_t)stream));
+}
+
+int beta_bin_sort(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                  const beta_opts* opt, const void* proj, uint32_t* pair_vals,
+                  int64_t pair_capacity, uint32_t* tile_ranges, int64_t* d_pair_count,
+                  int32_t* d_status, void* ws, size_t ws_bytes, beta_stream_t stream) {
+  if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !d_pair_count || !d_status)
+    return BETA_ERR_ARG;
+  if (pair_capacity < 0 || pair_capacity > 0x7fffffffll || (pair_capacity > 0 && !pair_vals))
+    return BETA_ERR_ARG;
+  int e = check_opts(opt);
+  if (e != BETA_OK) return e;
+  ViewTable vt;
+  if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  size_t need = binsort_ws_bytes((int64_t)prm->pitch * n_views, pair_capacity, vt.total_tiles);
+  if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u) != 0) return BETA_ERR_WORKSPACE;
+  ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
+  return cuda_status(launch_bin_sort(vt, prm->pitch, pb, pair_vals, pair_capacity, tile_ranges,
+                                     d_pair_count, d_status, ws, (cudaStream_t)stream));
+}
+
+int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                    const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
+                    const uint32_t* tile_ranges, float* color, float* T_final,
+                    uint32_t* n_contrib, const int32_t* d_status, beta_stream_t stream) {
+  if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !color || !T_final ||
+      !n_contrib || !d_status)
+    return BETA_ERR_ARG;
+  int e = check_opts(opt);
+  if (e != BETA_OK) return e;
+  ViewTable vt;
+  if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
+  return cuda_status(launch_raster_fwd(vt, render_opts(opt), pb.rec, pair_vals, tile_ranges, color,
+                                       T_final, n_contrib, d_status, (cudaStream_t)stream));
+}
+
+int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color, const float* target,
+                 float* loss, float* dL_dcolor, void* ws, size_t ws_bytes, beta_stream_t stream) {
+  if (!color || !target || !loss || !dL_dcolor) return BETA_ERR_ARG;
+  beta_opts o;
+  beta_default_opts(&o);
+  ViewTable vt;
+  int e = build_views(cams, n_views, &o, vt);
+  if (e != BETA_OK) return e;
+  if (!ws || ws_bytes < l1_ws_bytes(vt)) return BETA_ERR_WORKSPACE;
+  return cuda_status(launch_l1(vt, color, target, loss, dL_dcolor, (float*)ws, (cudaStream_t)stream));
+}
+
+int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                    const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
+                    const uint32_t* tile_ranges, const float* T_final,
+                    const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
+                    float* grad_planes, const int32_t* d_status, beta_stream_t stream) {
+  if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !T_final || !n_contrib ||
+      !dL_dcolor || !grad2d || !grad_planes || !d_status || !aligned16(grad2d))
+    return BETA_ERR_ARG;
+  int e = check_opts(opt);
+  if (e != BETA_OK) return e;
+  ViewTable vt;
+  if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  cudaStream_t s = (cudaStream_t)stream;
+  ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
+  RenderOpts ro = render_opts(opt);
+  cudaError_t ce = launch_zero(grad2d, (int64_t)prm->pitch * n_views * kGrad2d, s);
+  if (ce == cudaSuccess)
+    ce = launch_raster_bwd(vt, ro, pb.rec, pair_vals, tile_ranges, T_final, n_contrib, dL_dcolor,
+                           grad2d, d_status, s);
+  if (ce == cudaSuccess)
+    ce = launch_project_bwd(prm->planes, prm->n, prm->pitch, prm->n_lobes, vt, ro, grad2d,
+                            grad_planes, d_status, s);
+  return cuda_status(ce);
+}
+
+}  // extern "C"

@@ -1,0 +1,364 @@
+// beta_project.cu -- per-(view, primitive) projection (forward) and the chain
+// rule from 2D gradients back to the raw parameters (backward).
+//
+// Forward (Sec. 3.2 / Sec. 3.3 of arXiv 2501.18630), for primitive i, view v:
+//   s = exp(log-scale), q_hat = q/|q|, R = R(q_hat), t = W mu + t_w,
+//   J = d(pinhole)/dt, M = J W R S (2x3), Sigma' = M M^T + blur I,
+//   mu' = (fx tx/tz + cx, fy ty/tz + cy), o = sigmoid(logit), beta = 4 e^b,
+//   c = c0 + sum_m max(R_m . V, 0)^(4 e^{b_m}) c_m,  V = normalize(mu - campos).
+// One thread per primitive loops over the views, so the parameters are read
+// from HBM once per batch.
+//
+// Numerics: the tile rectangle and depth key follow the fixed fp32 rule in
+// beta_internal.cuh.  The projected centre is computed in double-float so
+// that the pixel offset x - mu' is exact to fp32 rounding; Sigma' is never
+// inverted directly: its Cholesky factor gives the whitening (p, q1, q2)
+// with r^2 = (p dx)^2 + (q2 dx + q1 dy)^2, and det Sigma' is the sum of the
+// squared 2x2 minors of M (Cauchy-Binet), each minor by Kahan's
+// difference-of-products.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "beta_internal.cuh"
+
+namespace beta {
+
+ProjBuffers proj_layout(void* proj, int32_t pitch, int32_t n_views) {
+  ProjBuffers b;
+  char* p = (char*)proj;
+  size_t nrec = (size_t)pitch * n_views;
+  b.rec = (float4*)p;
+  b.rect = (uint2*)(p + nrec * 64);
+  b.key = (uint32_t*)(p + nrec * 72);
+  return b;
+}
+
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+__device__ __forceinline__ float sigmoidf(float x) { return 1.0f / (1.0f + expf(-x)); }
+
+// log2(sigmoid(x)) without cancellation
+__device__ __forceinline__ float log2_sigmoid(float x) {
+  return x >= 0.0f ? -log1pf(expf(-x)) * kLog2e : x * kLog2e - log1pf(expf(x)) * kLog2e;
+}
+
+template <int M>
+__device__ __forceinline__ void load_params(const float* __restrict__ planes, int pitch, int i,
+                                            float* p, bool& ok) {
+  ok = true;
+#pragma unroll
+  for (int k = 0; k < 15 + 6 * M; ++k) {
+    p[k] = planes[(size_t)k * pitch + i];
+    ok = ok && isfinite(p[k]);
+  }
+}
+
+template <int M>
+__device__ __forceinline__ void sb_colour(const float* p, const ViewDev& V, int mode, float c[3]) {
+  c[0] = c[1] = c[2] = 0.0f;
+  if (mode != 2) {
+    c[0] = p[12];
+    c[1] = p[13];
+    c[2] = p[14];
+  }
+  if (M > 0 && mode != 1) {
+    float vx = p[0] - V.campos[0], vy = p[1] - V.campos[1], vz = p[2] - V.campos[2];
+    float inv = rsqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+    vx *= inv;
+    vy *= inv;
+    vz *= inv;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const float* L = p + 15 + 6 * m;
+      float st, ct, sp, cp;
+      sincosf(L[0], &st, &ct);
+      sincosf(L[1], &sp, &cp);
+      float dot = st * cp * vx + st * sp * vy + ct * vz;
+      if (dot > 0.0f) {
+        float w = exp2f(4.0f * expf(L[2]) * log2f(dot));
+        c[0] = fmaf(w, L[3], c[0]);
+        c[1] = fmaf(w, L[4], c[1]);
+        c[2] = fmaf(w, L[5], c[2]);
+      }
+    }
+  }
+}
+
+template <int M>
+__global__ void __launch_bounds__(256) k_project(const float* __restrict__ planes, int n, int pitch,
+                                                 ViewTable vt, RenderOpts ro,
+                                                 float4* __restrict__ rec, uint2* __restrict__ rect,
+                                                 uint32_t* __restrict__ key) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pitch) return;
+  float p[15 + 6 * M];
+  bool ok = false;
+  if (i < n) load_params<M>(planes, pitch, i, p, ok);
+  if (ok) ok = (p[11] >= ro.b_lo) && (p[11] < ro.b_hi);
+  for (int v = 0; v < vt.n_views; ++v) {
+    const ViewDev& V = vt.v[v];
+    const size_t r = (size_t)v * pitch + i;
+    Geo g;
+    int rc[4];
+    uint32_t kk = 0xffffffffu;
+    bool bin = ok && rule_chain(p, V, ro.blur_eps, g, rc, kk);
+    float4 o0, o1, o2, o3;
+    if (bin) {
+      // projected centre in double-float
+      dd tx = cam_coord_dd(V, 0, g.mu), ty = cam_coord_dd(V, 1, g.mu), tz = cam_coord_dd(V, 2, g.mu);
+      dd mx = dd_add_f(dd_mul_f(dd_div(tx, tz), V.fx), V.cx);
+      dd my = dd_add_f(dd_mul_f(dd_div(ty, tz), V.fy), V.cy);
+      float ix = floorf(mx.hi), iy = floorf(my.hi);
+      float fx = (mx.hi - ix) + mx.lo, fy = (my.hi - iy) + my.lo;
+      if (fx < 0.0f) { ix -= 1.0f; fx += 1.0f; }
+      if (fx >= 1.0f) { ix += 1.0f; fx -= 1.0f; }
+      if (fy < 0.0f) { iy -= 1.0f; fy += 1.0f; }
+      if (fy >= 1.0f) { iy += 1.0f; fy -= 1.0f; }
+      // Sigma' = M M^T + blur I, det by Cauchy-Binet
+      float a0 = fmaf(g.M0[0], g.M0[0], fmaf(g.M0[1], g.M0[1], g.M0[2] * g.M0[2]));
+      float c0 = fmaf(g.M1[0], g.M1[0], fmaf(g.M1[1], g.M1[1], g.M1[2] * g.M1[2]));
+      float b = fmaf(g.M0[0], g.M1[0], fmaf(g.M0[1], g.M1[1], g.M0[2] * g.M1[2]));
+      float m01 = diff_of_products(g.M0[0], g.M1[1], g.M0[1], g.M1[0]);
+      float m02 = diff_of_products(g.M0[0], g.M1[2], g.M0[2], g.M1[0]);
+      float m12 = diff_of_products(g.M0[1], g.M1[2], g.M0[2], g.M1[1]);
+      float det = fmaf(m01, m01, fmaf(m02, m02, m12 * m12));
+      float a = a0 + ro.blur_eps;
+      if (ro.blur_eps != 0.0f) det = fmaf(ro.blur_eps, a0 + c0 + ro.blur_eps, det);
+      bin = (det > 0.0f) && (a > 0.0f) && isfinite(det);
+      if (bin) {
+        float sa = sqrtf(a), sd = sqrtf(det);
+        float pp = 1.0f / sa;
+        float q1 = sa / sd;
+        float q2 = -(b * pp) / sd;
+        float beta = 4.0f * expf(p[11]);
+        float col[3];
+        sb_colour<M>(p, V, ro.color_mode, col);
+        const float INFL = 1.000244140625f, PAD = 0.015625f;
+        float ex = sqrtf(g.sxx) * INFL + PAD, ey = sqrtf(g.syy) * INFL + PAD;
+        o0 = make_float4(ix, iy, 0.5f - fx, 0.5f - fy);
+        o1 = make_float4(pp, q1, q2, beta);
+        o2 = make_float4(log2_sigmoid(p[10]), col[0], col[1], col[2]);
+        o3 = make_float4(ex, ey, sigmoidf(p[10]), 0.0f);
+      }
+    }
+    if (bin) {
+      rec[r * 4 + 0] = o0;
+      rec[r * 4 + 1] = o1;
+      rec[r * 4 + 2] = o2;
+      rec[r * 4 + 3] = o3;
+      rect[r] = make_uint2((uint32_t)rc[0] | ((uint32_t)rc[1] << 16), (uint32_t)rc[2] | ((uint32_t)rc[3] << 16));
+      key[r] = kk;
+    } else {
+      rect[r] = make_uint2(1u, 1u);
+      key[r] = 0xffffffffu;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// backward: 2D gradients (d mu', d Sigma' (a, b, c), d o, d beta, d colour)
+// of every view -> gradients of the raw parameters.
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ planes, int n,
+                                                     int pitch, ViewTable vt, RenderOpts ro,
+                                                     const float* __restrict__ grad2d,
+                                                     float* __restrict__ gout,
+                                                     const int32_t* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NP = 15 + 6 * M;
+  float gp[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) gp[k] = 0.0f;
+  float p[NP];
+  bool ok = false;
+  load_params<M>(planes, pitch, i, p, ok);
+  if (ok) ok = (p[11] >= ro.b_lo) && (p[11] < ro.b_hi);
+  if (*status != 0) ok = false;
+  if (ok) {
+    const float o = sigmoidf(p[10]);
+    const float beta = 4.0f * expf(p[11]);
+    for (int v = 0; v < vt.n_views; ++v) {
+      const ViewDev& V = vt.v[v];
+      const float* g2 = grad2d + ((size_t)v * pitch + i) * kGrad2d;
+      float G[kGrad2d];
+      bool any = false;
+#pragma unroll
+      for (int k = 0; k < kGrad2d; ++k) {
+        G[k] = g2[k];
+        any = any || (G[k] != 0.0f);
+      }
+      if (!any) continue;
+      Geo g;
+      int rc[4];
+      uint32_t kk;
+      if (!rule_chain(p, V, ro.blur_eps, g, rc, kk)) continue;
+      const float gmx = G[0], gmy = G[1], ga = G[2], gb = G[3], gc = G[4];
+      // Sigma' = M M^T: dM0 = 2 ga M0 + gb M1, dM1 = gb M0 + 2 gc M1
+      float dM0[3], dM1[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        dM0[k] = 2.0f * ga * g.M0[k] + gb * g.M1[k];
+        dM1[k] = gb * g.M0[k] + 2.0f * gc * g.M1[k];
+      }
+      // M0k = (j00 A0k + j02 A2k) s_k ; M1k = (j11 A1k + j12 A2k) s_k
+      float dA[9];
+      float dj00 = 0.f, dj02 = 0.f, dj11 = 0.f, dj12 = 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        float u0 = g.j00 * g.A[0 * 3 + k] + g.j02 * g.A[2 * 3 + k];
+        float u1 = g.j11 * g.A[1 * 3 + k] + g.j12 * g.A[2 * 3 + k];
+        float ds = dM0[k] * u0 + dM1[k] * u1;
+        gp[3 + k] += ds * g.s[k];                      // d log-scale
+        dA[0 * 3 + k] = dM0[k] * g.j00 * g.s[k];
+        dA[1 * 3 + k] = dM1[k] * g.j11 * g.s[k];
+        dA[2 * 3 + k] = (dM0[k] * g.j02 + dM1[k] * g.j12) * g.s[k];
+        dj00 += dM0[k] * g.A[0 * 3 + k] * g.s[k];
+        dj02 += dM0[k] * g.A[2 * 3 + k] * g.s[k];
+        dj11 += dM1[k] * g.A[1 * 3 + k] * g.s[k];
+        dj12 += dM1[k] * g.A[2 * 3 + k] * g.s[k];
+      }
+      // A = W Rq  ->  dRq = W^T dA
+      float dR[9];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          dR[a * 3 + c] = V.R[0 * 3 + a] * dA[0 * 3 + c] + V.R[1 * 3 + a] * dA[1 * 3 + c] +
+                          V.R[2 * 3 + a] * dA[2 * 3 + c];
+      // Rq(q_hat) -> d q_hat
+      const float w = g.q[0], x = g.q[1], y = g.q[2], z = g.q[3];
+      float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+      float dx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
+                        w * dR[7] - 2.f * x * dR[8]);
+      float dy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
+                        z * dR[7] - 2.f * y * dR[8]);
+      float dz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] +
+                        y * dR[5] + x * dR[6] + y * dR[7]);
+      float qd = w * dw + x * dx + y * dy + z * dz;
+      float iq = 1.0f / g.qn;
+      gp[6] += (dw - w * qd) * iq;
+      gp[7] += (dx - x * qd) * iq;
+      gp[8] += (dy - y * qd) * iq;
+      gp[9] += (dz - z * qd) * iq;
+      // J(t) and mu'(t)
+      const float tx = g.tc[0], ty = g.tc[1], iz = g.iz, iz2 = iz * iz, iz3 = iz2 * iz;
+      float dtx = dj02 * (-V.fx * iz2) + gmx * V.fx * iz;
+      float dty = dj12 * (-V.fy * iz2) + gmy * V.fy * iz;
+      float dtz = dj00 * (-V.fx * iz2) + dj11 * (-V.fy * iz2) + dj02 * (2.f * V.fx * tx * iz3) +
+                  dj12 * (2.f * V.fy * ty * iz3) - gmx * V.fx * tx * iz2 - gmy * V.fy * ty * iz2;
+      // t = W mu + t_w
+      gp[0] += V.R[0] * dtx + V.R[3] * dty + V.R[6] * dtz;
+      gp[1] += V.R[1] * dtx + V.R[4] * dty + V.R[7] * dtz;
+      gp[2] += V.R[2] * dtx + V.R[5] * dty + V.R[8] * dtz;
+      // opacity and shape
+      gp[10] += G[5] * o * (1.0f - o);
+      gp[11] += G[6] * beta;
+      // colour
+      const float gr = G[7], gg = G[8], gbl = G[9];
+      if (ro.color_mode != 2) {
+        gp[12] += gr;
+        gp[13] += gg;
+        gp[14] += gbl;
+      }
+      if (M > 0 && ro.color_mode != 1) {
+        float vx = p[0] - V.campos[0], vy = p[1] - V.campos[1], vz = p[2] - V.campos[2];
+        float len = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
+        float il = 1.0f / len;
+        vx *= il;
+        vy *= il;
+        vz *= il;
+        float dvx = 0.f, dvy = 0.f, dvz = 0.f;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const float* L = p + 15 + 6 * m;
+          float* dL = gp + 15 + 6 * m;
+          float st, ct, sp, cp;
+          sincosf(L[0], &st, &ct);
+          sincosf(L[1], &sp, &cp);
+          float rx = st * cp, ry = st * sp, rz = ct;
+          float dot = rx * vx + ry * vy + rz * vz;
+          if (dot > 0.0f) {
+            float bm = 4.0f * expf(L[2]);
+            float lw = log2f(dot);
+            float wgt = exp2f(bm * lw);
+            dL[3] += wgt * gr;
+            dL[4] += wgt * gg;
+            dL[5] += wgt * gbl;
+            float gw = gr * L[3] + gg * L[4] + gbl * L[5];
+            dL[2] += gw * wgt * (lw * kLn2) * bm;
+            float ddot = gw * bm * exp2f((bm - 1.0f) * lw);
+            float drx = ddot * vx, dry = ddot * vy, drz = ddot * vz;
+            dL[0] += drx * ct * cp + dry * ct * sp - drz * st;
+            dL[1] += -drx * st * sp + dry * st * cp;
+            dvx += ddot * rx;
+            dvy += ddot * ry;
+            dvz += ddot * rz;
+          }
+        }
+        float vd = vx * dvx + vy * dvy + vz * dvz;
+        gp[0] += (dvx - vx * vd) * il;
+        gp[1] += (dvy - vy * vd) * il;
+        gp[2] += (dvz - vz * vd) * il;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) gout[(size_t)k * pitch + i] = gp[k];
+}
+
+}  // namespace
+
+template <int M>
+static cudaError_t launch_project_m(const float* planes, int n, int pitch, const ViewTable& vt,
+                                    const RenderOpts& ro, ProjBuffers pb, cudaStream_t s) {
+  int grid = (pitch + 255) / 256;
+  if (grid < 1) return cudaSuccess;
+  k_project<M><<<grid, 256, 0, s>>>(planes, n, pitch, vt, ro, pb.rec, pb.rect, pb.key);
+  return cudaGetLastError();
+}
+
+template <int M>
+static cudaError_t launch_project_bwd_m(const float* planes, int n, int pitch, const ViewTable& vt,
+                                        const RenderOpts& ro, const float* grad2d, float* gout,
+                                        const int32_t* status, cudaStream_t s) {
+  int grid = (n + 255) / 256;
+  if (grid < 1) return cudaSuccess;
+  k_project_bwd<M><<<grid, 256, 0, s>>>(planes, n, pitch, vt, ro, grad2d, gout, status);
+  return cudaGetLastError();
+}
+
+#define BETA_DISPATCH_M(M_, CALL) \
+  switch (M_) {                   \
+    case 0: return CALL(0);       \
+    case 1: return CALL(1);       \
+    case 2: return CALL(2);       \
+    case 3: return CALL(3);       \
+    case 4: return CALL(4);       \
+    case 5: return CALL(5);       \
+    case 6: return CALL(6);       \
+    case 7: return CALL(7);       \
+    case 8: return CALL(8);       \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_project(const float* planes, int n, int pitch, int n_lobes, const ViewTable& vt,
+                           const RenderOpts& ro, ProjBuffers pb, cudaStream_t s) {
+#define CALL_P(m) launch_project_m<m>(planes, n, pitch, vt, ro, pb, s)
+  BETA_DISPATCH_M(n_lobes, CALL_P)
+#undef CALL_P
+}
+
+cudaError_t launch_project_bwd(const float* planes, int n, int pitch, int n_lobes,
+                               const ViewTable& vt, const RenderOpts& ro, const float* grad2d,
+                               float* grad_planes, const int32_t* status, cudaStream_t s) {
+#define CALL_B(m) launch_project_bwd_m<m>(planes, n, pitch, vt, ro, grad2d, grad_planes, status, s)
+  BETA_DISPATCH_M(n_lobes, CALL_B)
+#undef CALL_B
+}
+
+}  // namespace beta

@@ -1,0 +1,424 @@
+// beta_raster.cu -- tile compositing (forward), its reverse-order backward,
+// and the per-pixel L1 loss.
+//
+// Forward (Eq. C of arXiv 2501.18630): for every pixel of a 16x16 tile, walk
+// the tile's depth-sorted list, r^2 = (p dx)^2 + (q2 dx + q1 dy)^2, and for
+// r^2 < 1 (the Beta kernel's bounded support, Eq. 2) composite
+//   alpha = min(alpha_max, o (1 - r^2)^beta),  C += T alpha c,  T *= 1 - alpha,
+// stopping before a primitive once T < t_eps.
+//
+// Layout: one CTA of 256 threads per tile, one pixel per thread; warp w owns
+// the 8x4 pixel block (8 (w & 1), 4 (w >> 1)).  Records are staged 256 at a
+// time in shared memory together with an 8-bit mask of the warp blocks their
+// support box overlaps; each warp walks only the records of its mask bit
+// (ballot over 32 records), so whole warps skip records that cannot touch
+// them.  Transmittance early exit is decided per warp (__all_sync) and per
+// CTA (__syncthreads_or).
+//
+// Backward: the same tiling walks each tile list from the largest
+// last-contributor position down, recovering T_k = T_{k+1} / (1 - alpha_k)
+// and the suffix colour S (as g . S), and produces per-record 2D gradients
+// (d mu', d Sigma', d o, d beta, d colour).  A warp sums its 32 lanes'
+// 10 values with a 16-slot reduce-scatter butterfly (16 shuffles instead of
+// 50) and one atomic per value goes to the record's slot in grad2d.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "beta_internal.cuh"
+
+namespace beta {
+
+namespace {
+
+__device__ __forceinline__ uint8_t warp_mask(float4 f0, float4 f3, float tx0f, float ty0f) {
+  // centre relative to the tile origin, in pixel-index coordinates
+  float rx = (f0.x - tx0f) - f0.z;
+  float ry = (f0.y - ty0f) - f0.w;
+  float ex = f3.x, ey = f3.y;
+  uint32_t xm = 0, ym = 0;
+#pragma unroll
+  for (int cb = 0; cb < 2; ++cb) {
+    float bx = 8.0f * cb;
+    if (rx + ex >= bx && rx - ex <= bx + 7.0f) xm |= 1u << cb;
+  }
+#pragma unroll
+  for (int rb = 0; rb < 4; ++rb) {
+    float by = 4.0f * rb;
+    if (ry + ey >= by && ry - ey <= by + 3.0f) ym |= 1u << rb;
+  }
+  uint32_t m = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w)
+    if (((xm >> (w & 1)) & 1u) && ((ym >> (w >> 1)) & 1u)) m |= 1u << w;
+  return (uint8_t)m;
+}
+
+__global__ void __launch_bounds__(kThreads) k_raster_fwd(ViewTable vt, RenderOpts ro,
+                                                         const float4* __restrict__ rec,
+                                                         const uint32_t* __restrict__ vals,
+                                                         const uint32_t* __restrict__ ranges,
+                                                         float* __restrict__ color,
+                                                         float* __restrict__ Tout,
+                                                         uint32_t* __restrict__ ncontrib,
+                                                         const int32_t* __restrict__ status) {
+  __shared__ float4 s_rec[kThreads][3];
+  __shared__ uint8_t s_mask[kThreads];
+  if (*status != 0) return;
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int v = view_of_tile(vt, g);
+  const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
+  const int lt = g - vt.v[v].tile_off;
+  const int ty = lt / ntx, tx = lt - ty * ntx;
+  const int x = tx * 16 + (warp & 1) * 8 + (lane & 7);
+  const int y = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
+  const bool inside = x < W && y < H;
+  const float xf = (float)x, yf = (float)y;
+  const float tx0f = (float)(tx * 16), ty0f = (float)(ty * 16);
+  const uint32_t start = ranges[g], end = ranges[g + 1];
+  const float t_eps = ro.t_eps, amax = ro.alpha_max;
+
+  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+  uint32_t last = 0;
+  bool done = !inside;
+  bool warp_done = __all_sync(0xffffffffu, done);
+
+  for (uint32_t base = start; base < end; base += kThreads) {
+    if (!__syncthreads_or(!done)) break;
+    const uint32_t j = base + tid;
+    if (j < end) {
+      const uint32_t r = vals[j];
+      float4 f0 = rec[(size_t)r * 4 + 0];
+      float4 f1 = rec[(size_t)r * 4 + 1];
+      float4 f2 = rec[(size_t)r * 4 + 2];
+      float4 f3 = rec[(size_t)r * 4 + 3];
+      s_rec[tid][0] = f0;
+      s_rec[tid][1] = f1;
+      s_rec[tid][2] = f2;
+      s_mask[tid] = warp_mask(f0, f3, tx0f, ty0f);
+    }
+    __syncthreads();
+    const int cnt = (int)min((uint32_t)kThreads, end - base);
+    for (int c = 0; c < cnt && !warp_done; c += 32) {
+      const int idx = c + lane;
+      const bool bit = idx < cnt && ((s_mask[idx] >> warp) & 1u);
+      uint32_t bits = __ballot_sync(0xffffffffu, bit);
+      while (bits) {
+        const int k = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const int s = c + k;
+        const float4 f0 = s_rec[s][0];
+        const float4 f1 = s_rec[s][1];
+        const float dx = (xf - f0.x) + f0.z;
+        const float dy = (yf - f0.y) + f0.w;
+        const float u = f1.x * dx;
+        const float vv = fmaf(f1.z, dx, f1.y * dy);
+        const float r2 = fmaf(u, u, vv * vv);
+        if (!done && r2 < 1.0f) {
+          const float4 f2 = s_rec[s][2];
+          const float lb = lg2_approx(1.0f - r2);
+          float a = ex2_approx(fmaf(f1.w, lb, f2.x));
+          a = fminf(a, amax);
+          const float w = a * T;
+          C0 = fmaf(w, f2.y, C0);
+          C1 = fmaf(w, f2.z, C1);
+          C2 = fmaf(w, f2.w, C2);
+          T = T * (1.0f - a);
+          last = base - start + (uint32_t)s + 1u;
+          done = T < t_eps;
+        }
+      }
+      warp_done = __all_sync(0xffffffffu, done);
+    }
+  }
+  if (inside) {
+    const int64_t HW = (int64_t)W * H;
+    const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
+    float* cb = color + 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+    cb[0] = C0 + T * vt.v[v].bg[0];
+    cb[HW] = C1 + T * vt.v[v].bg[1];
+    cb[2 * HW] = C2 + T * vt.v[v].bg[2];
+    Tout[pix] = T;
+    ncontrib[pix] = last;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_raster_bwd(ViewTable vt, RenderOpts ro,
+                                                         const float4* __restrict__ rec,
+                                                         const uint32_t* __restrict__ vals,
+                                                         const uint32_t* __restrict__ ranges,
+                                                         const float* __restrict__ Tfin,
+                                                         const uint32_t* __restrict__ ncontrib,
+                                                         const float* __restrict__ dLdC,
+                                                         float* __restrict__ grad2d,
+                                                         const int32_t* __restrict__ status) {
+  __shared__ float4 s_rec[kThreads][4];
+  __shared__ uint8_t s_mask[kThreads];
+  __shared__ uint32_t s_ridx[kThreads];
+  __shared__ uint32_t s_wmax[kThreads / 32];
+  if (*status != 0) return;
+  const int g = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int v = view_of_tile(vt, g);
+  const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
+  const int lt = g - vt.v[v].tile_off;
+  const int ty = lt / ntx, tx = lt - ty * ntx;
+  const int x = tx * 16 + (warp & 1) * 8 + (lane & 7);
+  const int y = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
+  const bool inside = x < W && y < H;
+  const float xf = (float)x, yf = (float)y;
+  const float tx0f = (float)(tx * 16), ty0f = (float)(ty * 16);
+  const uint32_t start = ranges[g];
+  const float amax = ro.alpha_max;
+
+  float T = 1.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, GS = 0.0f;
+  uint32_t nl = 0;
+  if (inside) {
+    const int64_t HW = (int64_t)W * H;
+    const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
+    const float* gb = dLdC + 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+    gx = gb[0];
+    gy = gb[HW];
+    gz = gb[2 * HW];
+    T = Tfin[pix];
+    nl = ncontrib[pix];
+    GS = T * (gx * vt.v[v].bg[0] + gy * vt.v[v].bg[1] + gz * vt.v[v].bg[2]);
+  }
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, nl);
+  if (lane == 0) s_wmax[warp] = wmax;
+  __syncthreads();
+  uint32_t bmax = 0;
+#pragma unroll
+  for (int w = 0; w < kThreads / 32; ++w) bmax = max(bmax, s_wmax[w]);
+
+  for (int top = (int)bmax; top > 0; top -= kThreads) {
+    const int lo = max(0, top - kThreads);
+    const int cnt = top - lo;
+    __syncthreads();
+    if (tid < cnt) {
+      const uint32_t r = vals[start + lo + tid];
+      float4 f0 = rec[(size_t)r * 4 + 0];
+      float4 f1 = rec[(size_t)r * 4 + 1];
+      float4 f2 = rec[(size_t)r * 4 + 2];
+      float4 f3 = rec[(size_t)r * 4 + 3];
+      s_rec[tid][0] = f0;
+      s_rec[tid][1] = f1;
+      s_rec[tid][2] = f2;
+      s_rec[tid][3] = f3;
+      s_mask[tid] = warp_mask(f0, f3, tx0f, ty0f);
+      s_ridx[tid] = r;
+    }
+    __syncthreads();
+    for (int c = ((cnt - 1) >> 5) << 5; c >= 0; c -= 32) {
+      if ((uint32_t)(lo + c) >= wmax) continue;
+      const int idx = c + lane;
+      const bool bit = idx < cnt && ((s_mask[idx] >> warp) & 1u) && (uint32_t)(lo + idx) < wmax;
+      uint32_t bits = __ballot_sync(0xffffffffu, bit);
+      while (bits) {
+        const int k = 31 - __clz(bits);
+        bits &= ~(1u << k);
+        const int s = c + k;
+        const uint32_t pos = (uint32_t)(lo + s);
+        const float4 f0 = s_rec[s][0];
+        const float4 f1 = s_rec[s][1];
+        const float dx = (xf - f0.x) + f0.z;
+        const float dy = (yf - f0.y) + f0.w;
+        const float u = f1.x * dx;
+        const float vv = fmaf(f1.z, dx, f1.y * dy);
+        const float r2 = fmaf(u, u, vv * vv);
+        const bool act = pos < nl && r2 < 1.0f;
+        if (!__any_sync(0xffffffffu, act)) continue;
+        float G[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) G[q] = 0.0f;
+        if (act) {
+          const float4 f2 = s_rec[s][2];
+          const float4 f3 = s_rec[s][3];
+          const float beta = f1.w, o = f3.z;
+          const float base = 1.0f - r2;
+          const float lb = lg2_approx(base);
+          const float B = ex2_approx(beta * lb);
+          const float a0 = o * B;
+          const float a = fminf(a0, amax);
+          const float inv = __frcp_rn(1.0f - a);
+          const float Tk = T * inv;
+          const float gc = gx * f2.y + gy * f2.z + gz * f2.w;
+          const float dLa = Tk * gc - GS * inv;
+          GS = fmaf(a * Tk, gc, GS);
+          const float wgt = a * Tk;
+          G[7] = wgt * gx;
+          G[8] = wgt * gy;
+          G[9] = wgt * gz;
+          if (a0 < amax) {
+            G[5] = dLa * B;                                   // d o
+            G[6] = dLa * a0 * lb * 0.6931471805599453f;        // d beta
+            const float dr2 = -dLa * a0 * beta / base;
+            const float w0 = fmaf(f1.x, u, f1.z * vv);         // Sigma'^-1 d
+            const float w1 = f1.y * vv;
+            G[0] = -2.0f * dr2 * w0;                          // d mu'_x
+            G[1] = -2.0f * dr2 * w1;                          // d mu'_y
+            G[2] = -dr2 * w0 * w0;                            // d Sigma'_xx
+            G[3] = -2.0f * dr2 * w0 * w1;                     // d Sigma'_xy
+            G[4] = -dr2 * w1 * w1;                            // d Sigma'_yy
+          }
+          T = Tk;
+        }
+        // reduce-scatter butterfly over 16 slots
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const bool up = lane & 16;
+          const float send = up ? G[q] : G[q + 8];
+          const float keep = up ? G[q + 8] : G[q];
+          G[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const bool up = lane & 8;
+          const float send = up ? G[q] : G[q + 4];
+          const float keep = up ? G[q + 4] : G[q];
+          G[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const bool up = lane & 4;
+          const float send = up ? G[q] : G[q + 2];
+          const float keep = up ? G[q + 2] : G[q];
+          G[q] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        {
+          const bool up = lane & 2;
+          const float send = up ? G[0] : G[1];
+          const float keep = up ? G[1] : G[0];
+          G[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+        }
+        G[0] += __shfl_xor_sync(0xffffffffu, G[0], 1);
+        const int slot = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+        if (!(lane & 1) && slot < kGrad2d && G[0] != 0.0f)
+          atomicAdd(grad2d + (size_t)s_ridx[s] * kGrad2d + slot, G[0]);
+      }
+    }
+  }
+}
+
+__global__ void k_zero(float4* __restrict__ p, int64_t n4) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// L1 loss: one thread per pixel; block partial sums then a deterministic
+// per-view reduction.
+__global__ void __launch_bounds__(256) k_l1(ViewTable vt, const float* __restrict__ color,
+                                            const float* __restrict__ target, float* __restrict__ dLdC,
+                                            float* __restrict__ partial) {
+  __shared__ float s_w[8];
+  const int b = blockIdx.x;
+  int lo = 0, hi = vt.n_views - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (vt.v[mid].pad0 <= b) lo = mid; else hi = mid - 1;
+  }
+  const int v = lo;
+  const int64_t HW = (int64_t)vt.v[v].width * vt.v[v].height;
+  const int64_t p = (int64_t)(b - vt.v[v].pad0) * 256 + threadIdx.x;
+  float acc = 0.0f;
+  if (p < HW) {
+    const float scale = 1.0f / (3.0f * (float)HW);
+    const int64_t o = 3 * vt.v[v].pix_off + p;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      float d = color[o + ch * HW] - target[o + ch * HW];
+      acc += fabsf(d);
+      dLdC[o + ch * HW] = d > 0.0f ? scale : (d < 0.0f ? -scale : 0.0f);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < 8; ++w) t += s_w[w];
+    partial[b] = t;
+  }
+}
+
+__global__ void k_l1_reduce(ViewTable vt, const float* __restrict__ partial, int total_blocks,
+                            float* __restrict__ loss) {
+  __shared__ double s_w[32];
+  const int v = blockIdx.x;
+  const int b0 = vt.v[v].pad0;
+  const int b1 = (v + 1 < vt.n_views) ? vt.v[v + 1].pad0 : total_blocks;
+  double acc = 0.0;
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) acc += (double)partial[b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
+    const double HW = (double)vt.v[v].width * vt.v[v].height;
+    loss[v] = (float)(t / (3.0 * HW));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_raster_fwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
+                              const uint32_t* vals, const uint32_t* ranges, float* color,
+                              float* T_final, uint32_t* n_contrib, const int32_t* status,
+                              cudaStream_t s) {
+  if (vt.total_tiles <= 0) return cudaSuccess;
+  k_raster_fwd<<<vt.total_tiles, kThreads, 0, s>>>(vt, ro, rec, vals, ranges, color, T_final,
+                                                   n_contrib, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_raster_bwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
+                              const uint32_t* vals, const uint32_t* ranges, const float* T_final,
+                              const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
+                              const int32_t* status, cudaStream_t s) {
+  if (vt.total_tiles <= 0) return cudaSuccess;
+  k_raster_bwd<<<vt.total_tiles, kThreads, 0, s>>>(vt, ro, rec, vals, ranges, T_final, n_contrib,
+                                                   dL_dcolor, grad2d, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(float* p, int64_t n, cudaStream_t s) {
+  // n is a multiple of 4 (pitch % 4 == 0) and p is 16-byte aligned
+  if (n <= 0) return cudaSuccess;
+  int64_t n4 = n / 4;
+  int grid = (int)std::min<int64_t>((n4 + 255) / 256, 152 * 8);
+  k_zero<<<grid, 256, 0, s>>>((float4*)p, n4);
+  return cudaGetLastError();
+}
+
+// the L1 block offsets of each view ride in ViewDev::pad0
+static int l1_blocks(ViewTable& vt) {
+  int b = 0;
+  for (int v = 0; v < vt.n_views; ++v) {
+    vt.v[v].pad0 = b;
+    int64_t HW = (int64_t)vt.v[v].width * vt.v[v].height;
+    b += (int)((HW + 255) / 256);
+  }
+  return b;
+}
+
+size_t l1_ws_bytes(const ViewTable& vt) {
+  ViewTable t = vt;
+  return (size_t)l1_blocks(t) * sizeof(float);
+}
+
+cudaError_t launch_l1(const ViewTable& vt_in, const float* color, const float* target, float* loss,
+                      float* dL_dcolor, float* ws, cudaStream_t s) {
+  ViewTable vt = vt_in;
+  int nb = l1_blocks(vt);
+  if (nb <= 0) return cudaSuccess;
+  k_l1<<<nb, 256, 0, s>>>(vt, color, target, dL_dcolor, ws);
+  k_l1_reduce<<<vt.n_views, 256, 0, s>>>(vt, ws, nb, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace beta

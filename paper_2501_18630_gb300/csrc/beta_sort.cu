@@ -1,0 +1,501 @@
+// beta_sort.cu -- binning and depth ordering of (tile, record) pairs.
+//
+// Sec. 3.2 of arXiv 2501.18630 composites "after sorting overlapping
+// primitives by depth relative to the camera".  Here every record (view,
+// primitive) is first ordered by its depth key with a stable LSD radix sort;
+// the pairs (global tile, record) are then emitted in that order and sorted
+// stably by tile alone.  The result equals a sort of the pairs by
+// (tile, depth key, primitive index) while moving only 32-bit keys.
+//
+// Both radix sorts are onesweep sorts (one digit histogram pass for all
+// digits, then one scatter kernel per 8-bit digit whose CTAs chain their
+// digit offsets by decoupled look-back).  Every look-back wait is bounded:
+// after kSpinLimit polls the CTA records BETA_ERR_TIMEOUT and proceeds.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "beta_internal.cuh"
+
+namespace beta {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;                            // keys per thread
+constexpr int kSortTile = kSortThreads * kSortItems;     // 4096 keys per CTA tile
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kSortThreads * kScanItems;     // 2048 records per scan block
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kCountMask = (1u << 30) - 1;
+constexpr int kSpinLimit = 1 << 20;
+constexpr int kMaxPasses = 4;
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+// Workspace carve-up (offsets are 256-byte aligned).
+struct SortWs {
+  uint32_t* dkey_a;
+  uint32_t* dkey_b;
+  uint32_t* dval_a;
+  uint32_t* dval_b;
+  unsigned long long* bsum;
+  unsigned long long* boff;
+  uint32_t* pkey_a;
+  uint32_t* pkey_b;
+  uint32_t* pval_ws;
+  uint32_t* ghist;      // [2][kMaxPasses][256]: depth sort, tile sort
+  uint32_t* counters;   // [2][kMaxPasses] look-back tile counters
+  uint32_t* look_d;     // [4][nblk_d][256]
+  uint32_t* look_t;     // [npass_t][nblk_t][256]
+  size_t bytes;
+};
+
+static int tile_passes(int total_tiles) {
+  int bits = 0;
+  while ((1ll << bits) < (int64_t)total_tiles) ++bits;
+  return (bits + 7) / 8;
+}
+
+static SortWs carve(void* base, int64_t n_items, int64_t cap, int total_tiles) {
+  SortWs w{};
+  char* p = (char*)base;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* q = p ? p + off : nullptr;
+    off += align256(bytes);
+    return q;
+  };
+  int64_t nblk_d = cdiv(n_items, kSortTile);
+  int64_t nblk_t = cdiv(cap > 0 ? cap : 1, kSortTile);
+  int64_t nb_scan = cdiv(n_items, kScanTile);
+  int np_t = tile_passes(total_tiles);
+  w.dkey_a = (uint32_t*)take(n_items * 4);
+  w.dkey_b = (uint32_t*)take(n_items * 4);
+  w.dval_a = (uint32_t*)take(n_items * 4);
+  w.dval_b = (uint32_t*)take(n_items * 4);
+  w.bsum = (unsigned long long*)take(nb_scan * 8);
+  w.boff = (unsigned long long*)take(nb_scan * 8);
+  w.pkey_a = (uint32_t*)take(cap * 4);
+  w.pkey_b = (uint32_t*)take(cap * 4);
+  w.pval_ws = (uint32_t*)take(cap * 4);
+  w.ghist = (uint32_t*)take(2 * kMaxPasses * 256 * 4);
+  w.counters = (uint32_t*)take(2 * kMaxPasses * 4);
+  w.look_d = (uint32_t*)take((size_t)4 * nblk_d * 256 * 4);
+  w.look_t = (uint32_t*)take((size_t)(np_t > 0 ? np_t : 1) * nblk_t * 256 * 4);
+  w.bytes = off;
+  return w;
+}
+
+size_t binsort_ws_bytes(int64_t n_items, int64_t cap, int total_tiles) {
+  return carve(nullptr, n_items, cap, total_tiles).bytes;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_sort_prep(uint32_t* ghist, uint32_t* counters, int64_t* d_count, int32_t* status) {
+  int t = threadIdx.x;
+  for (int i = t; i < 2 * kMaxPasses * 256; i += blockDim.x) ghist[i] = 0;
+  if (t < 2 * kMaxPasses) counters[t] = 0;
+  if (t == 0) {
+    *d_count = 0;
+    *status = 0;
+  }
+}
+
+// Digit histograms of every pass at once; also clears the look-back table
+// of the sort (only the tiles that `count` needs).
+__global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __restrict__ keys,
+                                                             int64_t count_host,
+                                                             const int64_t* __restrict__ d_count,
+                                                             int64_t cap, int npass,
+                                                             uint32_t* __restrict__ ghist,
+                                                             uint32_t* __restrict__ look,
+                                                             int64_t look_stride_tiles) {
+  __shared__ uint32_t h[kMaxPasses][256];
+  int64_t count = d_count ? min(*d_count, cap) : count_host;
+  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  // clear the look-back entries of the tiles this sort will use
+  int64_t nblk = (count + kSortTile - 1) / kSortTile;
+  int64_t nclear = (int64_t)npass * look_stride_tiles * 256;
+  int64_t used = nblk * 256;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nclear;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i % (look_stride_tiles * 256) < used) look[i] = 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ((count + 31) & ~31ll);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    bool valid = i < count;
+    uint32_t k = valid ? keys[i] : 0u;
+    for (int p = 0; p < npass; ++p) {
+      uint32_t d = valid ? ((k >> (8 * p)) & 255u) : 256u;
+      uint32_t peers = __match_any_sync(0xffffffffu, d);
+      int leader = __ffs(peers) - 1;
+      if (valid && lane == leader) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) {
+    uint32_t c = (&h[0][0])[i];
+    if (c) atomicAdd(&ghist[i], c);
+  }
+}
+
+// One onesweep scatter pass over 8-bit digit `shift/8`.
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int write_keys,
+    const uint32_t* __restrict__ ghist, uint32_t* look, uint32_t* tile_counter, int64_t count_host,
+    const int64_t* __restrict__ d_count, int64_t cap, int shift, int32_t* status) {
+  __shared__ uint32_t s_whist[kSortThreads / 32][256];
+  __shared__ uint32_t s_gbase[256];
+  __shared__ uint32_t s_gexcl[256];
+  __shared__ uint32_t s_tile;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t count = d_count ? min(*d_count, cap) : count_host;
+  const int64_t nblk = (count + kSortTile - 1) / kSortTile;
+
+  // exclusive scan of the global digit histogram (once per CTA)
+  {
+    uint32_t c = ghist[tid];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_gbase[warp] = x;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_gbase[w];
+    s_gexcl[tid] = wpre + x - c;
+    __syncthreads();
+  }
+
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= nblk) break;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) s_whist[w][tid] = 0;
+    __syncthreads();
+
+    const int64_t seg = tile * kSortTile + (int64_t)warp * (32 * kSortItems);
+    uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      int64_t idx = seg + it * 32 + lane;
+      bool valid = idx < count;
+      key[it] = valid ? keys_in[idx] : 0xffffffffu;
+      val[it] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      int64_t idx = seg + it * 32 + lane;
+      bool valid = idx < count;
+      uint32_t d = valid ? ((key[it] >> shift) & 255u) : 256u;
+      uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+      int leader = __ffs(peers) - 1;
+      uint32_t base = valid ? s_whist[warp][d & 255u] : 0u;
+      __syncwarp();
+      if (valid && lane == leader) s_whist[warp][d] = base + (uint32_t)__popc(peers);
+      __syncwarp();
+      loc[it] = base + rank;
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, CTA total
+    uint32_t total = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+      uint32_t c = s_whist[w][tid];
+      s_whist[w][tid] = total;
+      total += c;
+    }
+    // decoupled look-back for digit `tid`
+    uint32_t* my = look + tile * 256 + tid;
+    uint32_t excl = 0;
+    if (tile == 0) {
+      atomicExch(my, kFlagInc | total);
+    } else {
+      atomicExch(my, kFlagAgg | total);
+      int64_t j = tile - 1;
+      while (j >= 0) {
+        volatile uint32_t* pj = look + j * 256 + tid;
+        uint32_t v = *pj;
+        int spins = 0;
+        while ((v & ~kCountMask) == 0u) {
+          if (++spins > kSpinLimit) {
+            set_status(status, BETA_ERR_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+          v = *pj;
+        }
+        excl += v & kCountMask;
+        if ((v & ~kCountMask) != kFlagAgg) break;  // inclusive prefix (or timeout)
+        --j;
+      }
+      atomicExch(my, kFlagInc | (excl + total));
+    }
+    s_gbase[tid] = s_gexcl[tid] + excl;
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      int64_t idx = seg + it * 32 + lane;
+      if (idx < count) {
+        uint32_t d = (key[it] >> shift) & 255u;
+        uint32_t pos = s_gbase[d] + s_whist[warp][d] + loc[it];
+        if (write_keys) keys_out[pos] = key[it];
+        vals_out[pos] = val[it];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ uint32_t rect_count(uint2 r) {
+  int tx0 = (int)(r.x & 0xffffu), tx1 = (int)(r.x >> 16);
+  int ty0 = (int)(r.y & 0xffffu), ty1 = (int)(r.y >> 16);
+  if (tx0 > tx1 || ty0 > ty1) return 0u;
+  return (uint32_t)(tx1 - tx0 + 1) * (uint32_t)(ty1 - ty0 + 1);
+}
+
+// block-wide exclusive scan of 64-bit values (256 threads)
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long x,
+                                                              unsigned long long* s_w,
+                                                              unsigned long long& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  unsigned long long pre = 0, tot = 0;
+  for (int w = 0; w < kSortThreads / 32; ++w) {
+    if (w < warp) pre += s_w[w];
+    tot += s_w[w];
+  }
+  total = tot;
+  __syncthreads();
+  return pre + inc - x;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_count_sums(const uint32_t* __restrict__ order,
+                                                             const uint2* __restrict__ rects,
+                                                             int64_t n_items,
+                                                             unsigned long long* __restrict__ bsum) {
+  __shared__ unsigned long long s_w[kSortThreads / 32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  unsigned long long s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t j = base + k;
+    if (j < n_items) s += rect_count(rects[order[j]]);
+  }
+  unsigned long long total;
+  block_excl_scan(s, s_w, total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_sums(const unsigned long long* __restrict__ bsum,
+                                                    int64_t nb, unsigned long long* __restrict__ boff,
+                                                    int64_t* d_count, int64_t cap, int32_t* status) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ unsigned long long s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < nb; c0 += 1024) {
+    int64_t i = c0 + threadIdx.x;
+    unsigned long long x = i < nb ? bsum[i] : 0ull;
+    unsigned long long inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    unsigned long long pre = 0, tot = 0;
+    for (int w = 0; w < 32; ++w) {
+      if (w < warp) pre += s_w[w];
+      tot += s_w[w];
+    }
+    unsigned long long carry = s_carry;
+    if (i < nb) boff[i] = carry + pre + inc - x;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = carry + tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    unsigned long long K = s_carry;
+    *d_count = (int64_t)K;
+    if ((int64_t)K > cap) set_status(status, BETA_ERR_CAPACITY);
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ order,
+                                                       const uint2* __restrict__ rects,
+                                                       int64_t n_items, int pitch, ViewTable vt,
+                                                       const unsigned long long* __restrict__ boff,
+                                                       uint32_t* __restrict__ pkey,
+                                                       uint32_t* __restrict__ pval, int64_t cap) {
+  __shared__ unsigned long long s_w[kSortThreads / 32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  uint32_t rec[kScanItems];
+  uint2 rc[kScanItems];
+  unsigned long long s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t j = base + k;
+    rec[k] = j < n_items ? order[j] : 0u;
+    rc[k] = j < n_items ? rects[rec[k]] : make_uint2(1u, 1u);
+    s += rect_count(rc[k]);
+  }
+  unsigned long long total;
+  unsigned long long off = boff[blockIdx.x] + block_excl_scan(s, s_w, total);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    uint32_t c = rect_count(rc[k]);
+    if (c == 0) continue;
+    int v = (int)(rec[k] / (uint32_t)pitch);
+    int ntx = vt.v[v].ntx, toff = vt.v[v].tile_off;
+    int tx0 = (int)(rc[k].x & 0xffffu), tx1 = (int)(rc[k].x >> 16);
+    int ty0 = (int)(rc[k].y & 0xffffu), ty1 = (int)(rc[k].y >> 16);
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) {
+        if ((int64_t)off < cap) {
+          pkey[off] = (uint32_t)(toff + ty * ntx + tx);
+          pval[off] = rec[k];
+        }
+        ++off;
+      }
+  }
+}
+
+__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, const int64_t* __restrict__ d_count,
+                              int64_t cap, int total_tiles, uint32_t* __restrict__ ranges) {
+  const int64_t K = min(*d_count, cap);
+  if (K == 0) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g <= total_tiles;
+         g += (int64_t)gridDim.x * blockDim.x)
+      ranges[g] = 0u;
+    return;
+  }
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = keys[k];
+    int64_t prev = k > 0 ? (int64_t)keys[k - 1] : -1;
+    for (int64_t g = prev + 1; g <= t; ++g) ranges[g] = (uint32_t)k;
+    if (k == K - 1)
+      for (int64_t g = t + 1; g <= total_tiles; ++g) ranges[g] = (uint32_t)K;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launcher
+// ---------------------------------------------------------------------------
+
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint32_t* pair_vals,
+                            int64_t cap, uint32_t* ranges, int64_t* d_count, int32_t* d_status,
+                            void* ws, cudaStream_t s) {
+  const int64_t n_items = (int64_t)vt.n_views * pitch;
+  const int total_tiles = vt.total_tiles;
+  SortWs w = carve(ws, n_items, cap, total_tiles);
+  const int64_t nblk_d = cdiv(n_items, kSortTile);
+  const int64_t nblk_t = cdiv(cap > 0 ? cap : 1, kSortTile);
+  const int np_t = tile_passes(total_tiles);
+  const int persist = sm_count() * 4;
+  uint32_t* gh_d = w.ghist;
+  uint32_t* gh_t = w.ghist + kMaxPasses * 256;
+
+  k_sort_prep<<<1, 256, 0, s>>>(w.ghist, w.counters, d_count, d_status);
+
+  // 1. stable sort of all records by depth key (4 passes of 8 bits)
+  int grid_h = (int)std::min<int64_t>(cdiv(n_items, kSortThreads), (int64_t)persist * 2);
+  if (grid_h < 1) grid_h = 1;
+  k_digit_hist<<<grid_h, kSortThreads, 0, s>>>(pb.key, n_items, nullptr, n_items, 4, gh_d, w.look_d,
+                                               nblk_d);
+  const uint32_t* kin = pb.key;
+  const uint32_t* vin = nullptr;
+  uint32_t* kbuf[2] = {w.dkey_a, w.dkey_b};
+  uint32_t* vbuf[2] = {w.dval_a, w.dval_b};
+  int grid_d = (int)std::min<int64_t>(nblk_d, persist);
+  if (grid_d < 1) grid_d = 1;
+  for (int p = 0; p < 4; ++p) {
+    k_onesweep<<<grid_d, kSortThreads, 0, s>>>(kin, vin, kbuf[p & 1], vbuf[p & 1], p < 3 ? 1 : 0,
+                                               gh_d + p * 256, w.look_d + (size_t)p * nblk_d * 256,
+                                               w.counters + p, n_items, nullptr, n_items, 8 * p,
+                                               d_status);
+    kin = kbuf[p & 1];
+    vin = vbuf[p & 1];
+  }
+  const uint32_t* order = vbuf[1];
+
+  // 2. pair counts in depth order -> offsets -> emit (tile, record) pairs
+  const int64_t nb_scan = cdiv(n_items, kScanTile);
+  // final tile-sorted values must land in pair_vals: choose the emit buffer by pass parity
+  uint32_t* pval_emit = (np_t % 2 == 0) ? pair_vals : w.pval_ws;
+  uint32_t* pval_other = (np_t % 2 == 0) ? w.pval_ws : pair_vals;
+  if (nb_scan > 0) {
+    k_count_sums<<<(unsigned)nb_scan, kSortThreads, 0, s>>>(order, pb.rect, n_items, w.bsum);
+    k_scan_sums<<<1, 1024, 0, s>>>(w.bsum, nb_scan, w.boff, d_count, cap, d_status);
+    k_emit<<<(unsigned)nb_scan, kSortThreads, 0, s>>>(order, pb.rect, n_items, pitch, vt, w.boff,
+                                                       w.pkey_a, pval_emit, cap);
+  }
+
+  // 3. stable sort of the pairs by global tile id
+  const uint32_t* final_keys = w.pkey_a;
+  if (np_t > 0) {
+    int grid_th = (int)std::min<int64_t>(cdiv(cap, kSortThreads), (int64_t)persist * 2);
+    if (grid_th < 1) grid_th = 1;
+    k_digit_hist<<<grid_th, kSortThreads, 0, s>>>(w.pkey_a, 0, d_count, cap, np_t, gh_t, w.look_t,
+                                                  nblk_t);
+    int grid_t = (int)std::min<int64_t>(nblk_t, persist);
+    if (grid_t < 1) grid_t = 1;
+    uint32_t* pk[2] = {w.pkey_b, w.pkey_a};
+    uint32_t* pv[2] = {pval_other, pval_emit};
+    const uint32_t* ki = w.pkey_a;
+    const uint32_t* vi = pval_emit;
+    for (int p = 0; p < np_t; ++p) {
+      k_onesweep<<<grid_t, kSortThreads, 0, s>>>(ki, vi, pk[p & 1], pv[p & 1], 1,
+                                                 gh_t + p * 256, w.look_t + (size_t)p * nblk_t * 256,
+                                                 w.counters + kMaxPasses + p, 0, d_count, cap, 8 * p,
+                                                 d_status);
+      ki = pk[p & 1];
+      vi = pv[p & 1];
+    }
+    final_keys = ki;
+  }
+  int grid_r = (int)std::min<int64_t>(cdiv(std::max<int64_t>(cap, total_tiles + 1), 256), (int64_t)persist * 2);
+  if (grid_r < 1) grid_r = 1;
+  k_tile_ranges<<<grid_r, 256, 0, s>>>(final_keys, d_count, cap, total_tiles, ranges);
+  return cudaGetLastError();
+}
+
+}  // namespace beta

@@ -1,0 +1,171 @@
+"""PyTorch-side plumbing of the Beta rasterizer: device buffers, stream
+handles and a torch.autograd.Function.  All arithmetic runs in
+libbetasplat.so; this module only allocates memory and passes pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import torch
+
+from . import _lib
+from .scenes import n_planes
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Rasterizer:
+    """Buffers and launches of project -> bin/sort -> raster fwd/bwd for one
+    batch of views.  One forward may be in flight per instance: a second
+    forward overwrites the saved per-pixel state of the first."""
+
+    def __init__(self, n, pitch, n_lobes, cameras, opts: _lib.BetaOpts | None = None,
+                 pair_capacity: int | None = None, device="cuda"):
+        self.L = _lib.load()
+        self.n, self.pitch, self.n_lobes = int(n), int(pitch), int(n_lobes)
+        self.cameras = list(cameras)
+        self.V = len(self.cameras)
+        self.cams = _lib.make_cameras(self.cameras)
+        self.opts = opts or _lib.default_opts()
+        self.device = torch.device(device)
+        L = self.L
+        self.total_tiles = int(L.beta_total_tiles(self.cams, self.V, ctypes.byref(self.opts)))
+        self.total_pixels = int(L.beta_total_pixels(self.cams, self.V))
+        if self.total_tiles < 0 or self.total_pixels < 0:
+            raise ValueError("invalid cameras or options")
+        self.pix_off = []
+        off = 0
+        for c in self.cameras:
+            self.pix_off.append(off)
+            off += c.width * c.height
+        dev = self.device
+        self.proj = torch.empty(int(L.beta_proj_bytes(self.pitch, self.V)), dtype=torch.uint8, device=dev)
+        self.ranges = torch.empty(self.total_tiles + 1, dtype=torch.int32, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.color = torch.empty(3 * self.total_pixels, dtype=torch.float32, device=dev)
+        self.T_final = torch.empty(self.total_pixels, dtype=torch.float32, device=dev)
+        self.n_contrib = torch.empty(self.total_pixels, dtype=torch.int32, device=dev)
+        self.grad2d = torch.empty(int(L.beta_grad2d_bytes(self.pitch, self.V)) // 4, dtype=torch.float32, device=dev)
+        self.loss = torch.zeros(self.V, dtype=torch.float32, device=dev)
+        self.dL_dcolor = torch.empty_like(self.color)
+        self.l1_ws = torch.empty(max(4, int(L.beta_l1_workspace_bytes(self.cams, self.V))), dtype=torch.uint8, device=dev)
+        cap = pair_capacity if pair_capacity is not None else max(1 << 16, 4 * self.n * self.V)
+        self._alloc_pairs(cap)
+
+    # -- buffers -----------------------------------------------------------
+    def _alloc_pairs(self, cap: int):
+        cap = int(min(cap, 0x7FFFFFFF))
+        self.cap = cap
+        self.pair_vals = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)
+        ws = int(self.L.beta_binsort_workspace_bytes(self.pitch, self.V, cap, self.cams, ctypes.byref(self.opts)))
+        self.sort_ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
+
+    def params(self, planes: torch.Tensor) -> _lib.BetaParams:
+        assert planes.is_cuda and planes.dtype == torch.float32 and planes.is_contiguous()
+        assert planes.shape == (n_planes(self.n_lobes), self.pitch), planes.shape
+        return _lib.make_params(self.n, self.pitch, self.n_lobes, planes.data_ptr())
+
+    def image(self, buf: torch.Tensor, v: int) -> torch.Tensor:
+        """View v of a planar colour-like buffer as (3, H, W)."""
+        c = self.cameras[v]
+        o = 3 * self.pix_off[v]
+        return buf[o:o + 3 * c.width * c.height].view(3, c.height, c.width)
+
+    def plane(self, buf: torch.Tensor, v: int) -> torch.Tensor:
+        c = self.cameras[v]
+        o = self.pix_off[v]
+        return buf[o:o + c.width * c.height].view(c.height, c.width)
+
+    # -- the four steps ----------------------------------------------------
+    def project(self, planes):
+        prm = self.params(planes)
+        _lib.check("beta_project", self.L.beta_project(ctypes.byref(prm), self.cams, self.V,
+                                                        ctypes.byref(self.opts), _vp(self.proj), _stream()))
+
+    def bin_sort(self, planes):
+        prm = self.params(planes)
+        _lib.check("beta_bin_sort", self.L.beta_bin_sort(
+            ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
+            _vp(self.pair_vals), self.cap, _vp(self.ranges), _vp(self.count), _vp(self.status),
+            _vp(self.sort_ws), self.sort_ws.numel(), _stream()))
+
+    def raster_fwd(self, planes):
+        prm = self.params(planes)
+        _lib.check("beta_raster_fwd", self.L.beta_raster_fwd(
+            ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
+            _vp(self.pair_vals), _vp(self.ranges), _vp(self.color), _vp(self.T_final),
+            _vp(self.n_contrib), _vp(self.status), _stream()))
+
+    def l1_loss(self, target: torch.Tensor):
+        assert target.numel() == self.color.numel() and target.is_contiguous()
+        _lib.check("beta_l1_loss", self.L.beta_l1_loss(
+            self.cams, self.V, _vp(self.color), _vp(target), _vp(self.loss), _vp(self.dL_dcolor),
+            _vp(self.l1_ws), self.l1_ws.numel(), _stream()))
+        return self.loss, self.dL_dcolor
+
+    def raster_bwd(self, planes, dL_dcolor, grad_planes):
+        prm = self.params(planes)
+        assert grad_planes.shape == planes.shape and grad_planes.is_contiguous()
+        assert dL_dcolor.numel() == self.color.numel() and dL_dcolor.is_contiguous()
+        _lib.check("beta_raster_bwd", self.L.beta_raster_bwd(
+            ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
+            _vp(self.pair_vals), _vp(self.ranges), _vp(self.T_final), _vp(self.n_contrib),
+            _vp(dL_dcolor), _vp(self.grad2d), _vp(grad_planes), _vp(self.status), _stream()))
+
+    # -- composite calls ---------------------------------------------------
+    def device_status(self):
+        """(status, pair count); synchronises the current stream."""
+        torch.cuda.current_stream().synchronize()
+        return int(self.status.item()), int(self.count.item())
+
+    def forward(self, planes, check_capacity: bool = True):
+        """project + bin/sort + raster.  With check_capacity the pair count is
+        read back (one host sync) and the pair buffers grow if needed."""
+        self.project(planes)
+        self.bin_sort(planes)
+        if check_capacity:
+            st, k = self.device_status()
+            if st == _lib.BETA_ERR_CAPACITY:
+                self._alloc_pairs(int(math.ceil(k * 1.25)) + 1024)
+                self.bin_sort(planes)
+                st, k = self.device_status()
+            if st != _lib.BETA_OK:
+                raise _lib.BetaError("beta_bin_sort", st, self.L.beta_status_string(st).decode())
+        self.raster_fwd(planes)
+        return self.color
+
+    def backward(self, planes, dL_dcolor, grad_planes=None):
+        if grad_planes is None:
+            grad_planes = torch.zeros_like(planes)
+        self.raster_bwd(planes, dL_dcolor, grad_planes)
+        return grad_planes
+
+
+class BetaRasterize(torch.autograd.Function):
+    """colour = BetaRasterize.apply(planes, rasterizer): planar colour of every
+    view (3 * total_pixels).  Backward returns d loss / d planes."""
+
+    @staticmethod
+    def forward(ctx, planes, rast: Rasterizer):
+        color = rast.forward(planes).clone()
+        ctx.rast = rast
+        ctx.save_for_backward(planes)
+        return color
+
+    @staticmethod
+    def backward(ctx, gcolor):
+        (planes,) = ctx.saved_tensors
+        grad = ctx.rast.backward(planes, gcolor.contiguous())
+        return grad, None
+
+
+def render(planes, rast: Rasterizer):
+    return BetaRasterize.apply(planes, rast)

@@ -1,0 +1,107 @@
+"""The C-ABI library builds, loads and exports every symbol include/*.h
+declares; host-only queries and argument checks work without a GPU."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import pytest
+
+from paper_2501_18630_gb300 import _lib, build, scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return _lib.load()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(beta_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_symbols()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(L, name), name
+    assert set(_lib.EXPORTS) <= set(names)
+
+
+def test_header_prototypes_match_binding(L):
+    # the binding declares every exported entry point
+    for name in declared_symbols():
+        assert getattr(L, name).argtypes is not None or name in ("beta_version",), name
+
+
+def test_host_queries(L):
+    o = _lib.default_opts()
+    assert (o.tile_w, o.tile_h, o.batch_s, o.color_mode) == (16, 16, 256, 0)
+    assert o.t_eps == pytest.approx(2.0 ** -19) and o.alpha_max == pytest.approx(0.99)
+    assert math.isinf(o.b_lo) and o.b_lo < 0 and math.isinf(o.b_hi)
+    assert L.beta_version() >= 1
+    cams = [scenes.pinhole(*scenes.look_at((0, 0, -3)), 1297, 840),
+            scenes.pinhole(*scenes.look_at((0, 0, -3)), 256, 256)]
+    arr = _lib.make_cameras(cams)
+    assert L.beta_total_tiles(arr, 2, ctypes.byref(o)) == 82 * 53 + 16 * 16
+    assert L.beta_total_pixels(arr, 2) == 1297 * 840 + 256 * 256
+    assert L.beta_proj_bytes(1024, 3) == 1024 * 3 * 76
+    assert L.beta_grad2d_bytes(1024, 2) == 1024 * 2 * 40
+    assert L.beta_binsort_workspace_bytes(1024, 2, 10000, arr, ctypes.byref(o)) > 0
+    assert L.beta_l1_workspace_bytes(arr, 2) >= 4 * ((1297 * 840 + 255) // 256)
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert L.beta_status_string(code)
+
+
+def test_argument_errors_are_returned_without_launch(L):
+    o = _lib.default_opts()
+    cams = _lib.make_cameras([scenes.pinhole(*scenes.look_at((0, 0, -3)), 64, 64)])
+    prm = _lib.make_params(10, 32, 1, 0x1000)
+    # null projection buffer
+    assert L.beta_project(ctypes.byref(prm), cams, 1, ctypes.byref(o), None, None) == _lib.BETA_ERR_ARG
+    # pitch not a multiple of 4
+    bad = _lib.make_params(10, 30, 1, 0x1000)
+    assert L.beta_project(ctypes.byref(bad), cams, 1, ctypes.byref(o), ctypes.c_void_p(0x2000), None) == _lib.BETA_ERR_ARG
+    # too many lobes
+    bad = _lib.make_params(10, 32, 9, 0x1000)
+    assert L.beta_project(ctypes.byref(bad), cams, 1, ctypes.byref(o), ctypes.c_void_p(0x2000), None) == _lib.BETA_ERR_ARG
+    # unsupported tile shape
+    o2 = _lib.default_opts(tile_w=8)
+    assert L.beta_project(ctypes.byref(prm), cams, 1, ctypes.byref(o2), ctypes.c_void_p(0x2000), None) == _lib.BETA_ERR_UNSUPPORTED
+    # zero views
+    assert L.beta_project(ctypes.byref(prm), cams, 0, ctypes.byref(o), ctypes.c_void_p(0x2000), None) == _lib.BETA_ERR_ARG
+    # workspace too small
+    vp = ctypes.c_void_p(0x2000)
+    r = L.beta_bin_sort(ctypes.byref(prm), cams, 1, ctypes.byref(o), vp, vp, 100, vp, vp, vp, vp, 16, None)
+    assert r == _lib.BETA_ERR_WORKSPACE
+    # capacity beyond 2^31 - 1
+    r = L.beta_bin_sort(ctypes.byref(prm), cams, 1, ctypes.byref(o), vp, vp, 1 << 31, vp, vp, vp, vp, 1 << 40, None)
+    assert r == _lib.BETA_ERR_ARG
+    # invalid alpha_max
+    o3 = _lib.default_opts(alpha_max=1.0)
+    assert L.beta_project(ctypes.byref(prm), cams, 1, ctypes.byref(o3), vp, None) == _lib.BETA_ERR_ARG
+
+
+def test_product_path_has_no_cpu_fallback():
+    """The package never imports the oracle, and the binding raises when the
+    library file is absent."""
+    pkg = os.path.join(ROOT, "paper_2501_18630_gb300")
+    for f in glob.glob(os.path.join(pkg, "*.py")):
+        src = open(f).read()
+        assert "import oracle" not in src and "from oracle" not in src, f
+    with pytest.raises(RuntimeError):
+        saved = _lib._lib
+        try:
+            _lib._lib = None
+            _lib.load(os.path.join(ROOT, "does-not-exist.so"))
+        finally:
+            _lib._lib = saved
