@@ -169,21 +169,30 @@ int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color,
                  const float* target, float* loss, float* dL_dcolor, void* ws, size_t ws_bytes,
                  beta_stream_t stream);
 
-/* Step 4: reverse-order backward of Eq. C through the projection to the raw
- * parameters.  Walks each pixel's list from its last contributor down,
- * recovering T by division, accumulates per-record 2D gradients
- * (d mu', d Sigma', d o, d beta, d colour) with warp-reduced atomics into
- * grad2d, then chains them through Sec. 3.2/3.3 to every raw parameter and
- * sums over views.
- *   dL_dcolor  [3 x total_pixels] in
- *   grad2d     workspace of beta_grad2d_bytes() (overwritten)
- *   grad_planes out: (15 + 6M) x pitch float32, same layout as the params,
- *              overwritten for i < n (padding lanes are left untouched). */
+/* Step 4a (backward of Eq. C): walks each pixel's list from its last
+ * contributor down, recovering T by division, and accumulates per-record 2D
+ * gradients (d mu' (2), d Sigma' (a, b, c), d o, d beta, d colour (3)) with
+ * warp-reduced atomics into grad2d.
+ *   dL_dcolor [3 x total_pixels] in (layout of color)
+ *   grad2d    [beta_grad2d_bytes()] in/out: 10 floats per record, ACCUMULATED.
+ *             It must hold zeros on entry: zero it once after allocation;
+ *             beta_project_bwd clears every slot it consumes. */
 int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
                     const uint32_t* tile_ranges, const float* T_final,
                     const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
-                    float* grad_planes, const int32_t* d_status, beta_stream_t stream);
+                    const int32_t* d_status, beta_stream_t stream);
+
+/* Step 4b (backward of Sec. 3.2 / Sec. 3.3): chains the 2D gradients of every
+ * view through Sigma' = M M^T, M = J W R(q) S, mu'(t), t = W mu + t_w, the
+ * sigmoid, beta = 4 e^b and the spherical-Beta colour to the raw parameters,
+ * summing over views, then writes zeros back into grad2d.
+ *   grad_planes out: (15 + 6M) x pitch float32, same layout as the params,
+ *             overwritten for i < n (padding lanes are left untouched).
+ *   d_status  in: if non-zero, the gradients are written as zeros. */
+int beta_project_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                     const beta_opts* opt, float* grad2d, float* grad_planes,
+                     const int32_t* d_status, beta_stream_t stream);
 
 #ifdef __cplusplus
 }

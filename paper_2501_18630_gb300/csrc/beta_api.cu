@@ -229,25 +229,32 @@ int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
                     const uint32_t* tile_ranges, const float* T_final,
                     const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
-                    float* grad_planes, const int32_t* d_status, beta_stream_t stream) {
+                    const int32_t* d_status, beta_stream_t stream) {
   if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !T_final || !n_contrib ||
-      !dL_dcolor || !grad2d || !grad_planes || !d_status || !aligned16(grad2d))
+      !dL_dcolor || !grad2d || !d_status || !aligned16(grad2d))
     return BETA_ERR_ARG;
   int e = check_opts(opt);
   if (e != BETA_OK) return e;
   ViewTable vt;
   if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
-  cudaStream_t s = (cudaStream_t)stream;
   ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
-  RenderOpts ro = render_opts(opt);
-  cudaError_t ce = launch_zero(grad2d, (int64_t)prm->pitch * n_views * kGrad2d, s);
-  if (ce == cudaSuccess)
-    ce = launch_raster_bwd(vt, ro, pb.rec, pair_vals, tile_ranges, T_final, n_contrib, dL_dcolor,
-                           grad2d, d_status, s);
-  if (ce == cudaSuccess)
-    ce = launch_project_bwd(prm->planes, prm->n, prm->pitch, prm->n_lobes, vt, ro, grad2d,
-                            grad_planes, d_status, s);
-  return cuda_status(ce);
+  return cuda_status(launch_raster_bwd(vt, render_opts(opt), pb.rec, pair_vals, tile_ranges,
+                                       T_final, n_contrib, dL_dcolor, grad2d, d_status,
+                                       (cudaStream_t)stream));
+}
+
+int beta_project_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                     const beta_opts* opt, float* grad2d, float* grad_planes,
+                     const int32_t* d_status, beta_stream_t stream) {
+  if (!valid_params(prm) || !grad2d || !grad_planes || !d_status || !aligned16(grad2d))
+    return BETA_ERR_ARG;
+  int e = check_opts(opt);
+  if (e != BETA_OK) return e;
+  ViewTable vt;
+  if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  return cuda_status(launch_project_bwd(prm->planes, prm->n, prm->pitch, prm->n_lobes, vt,
+                                        render_opts(opt), grad2d, grad_planes, d_status,
+                                        (cudaStream_t)stream));
 }
 
 }  // extern "C"

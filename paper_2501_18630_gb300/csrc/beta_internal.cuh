@@ -287,7 +287,7 @@ ProjBuffers proj_layout(void* proj, int32_t pitch, int32_t n_views);
 cudaError_t launch_project(const float* planes, int n, int pitch, int n_lobes, const ViewTable& vt,
                            const RenderOpts& ro, ProjBuffers pb, cudaStream_t s);
 cudaError_t launch_project_bwd(const float* planes, int n, int pitch, int n_lobes,
-                               const ViewTable& vt, const RenderOpts& ro, const float* grad2d,
+                               const ViewTable& vt, const RenderOpts& ro, float* grad2d,
                                float* grad_planes, const int32_t* status, cudaStream_t s);
 
 struct SortWs;  // defined in beta_sort.cu
@@ -304,7 +304,6 @@ cudaError_t launch_raster_bwd(const ViewTable& vt, const RenderOpts& ro, const f
                               const uint32_t* vals, const uint32_t* ranges, const float* T_final,
                               const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
                               const int32_t* status, cudaStream_t s);
-cudaError_t launch_zero(float* p, int64_t n, cudaStream_t s);
 size_t l1_ws_bytes(const ViewTable& vt);
 cudaError_t launch_l1(const ViewTable& vt, const float* color, const float* target, float* loss,
                       float* dL_dcolor, float* ws, cudaStream_t s);

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
 template <int M>
 __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ planes, int n,
                                                      int pitch, ViewTable vt, RenderOpts ro,
-                                                     const float* __restrict__ grad2d,
+                                                     float* __restrict__ grad2d,
                                                      float* __restrict__ gout,
                                                      const int32_t* __restrict__ status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
     const float beta = 4.0f * expf(p[11]);
     for (int v = 0; v < vt.n_views; ++v) {
       const ViewDev& V = vt.v[v];
-      const float* g2 = grad2d + ((size_t)v * pitch + i) * kGrad2d;
+      float* g2 = grad2d + ((size_t)v * pitch + i) * kGrad2d;
       float G[kGrad2d];
       bool any = false;
 #pragma unroll
@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
         any = any || (G[k] != 0.0f);
       }
       if (!any) continue;
+      // leave the accumulator zeroed for the next backward
+#pragma unroll
+      for (int k = 0; k < kGrad2d; ++k) g2[k] = 0.0f;
       Geo g;
       int rc[4];
       uint32_t kk;
@@ -324,7 +327,7 @@ static cudaError_t launch_project_m(const float* planes, int n, int pitch, const
 
 template <int M>
 static cudaError_t launch_project_bwd_m(const float* planes, int n, int pitch, const ViewTable& vt,
-                                        const RenderOpts& ro, const float* grad2d, float* gout,
+                                        const RenderOpts& ro, float* grad2d, float* gout,
                                         const int32_t* status, cudaStream_t s) {
   int grid = (n + 255) / 256;
   if (grid < 1) return cudaSuccess;
@@ -354,7 +357,7 @@ cudaError_t launch_project(const float* planes, int n, int pitch, int n_lobes, c
 }
 
 cudaError_t launch_project_bwd(const float* planes, int n, int pitch, int n_lobes,
-                               const ViewTable& vt, const RenderOpts& ro, const float* grad2d,
+                               const ViewTable& vt, const RenderOpts& ro, float* grad2d,
                                float* grad_planes, const int32_t* status, cudaStream_t s) {
 #define CALL_B(m) launch_project_bwd_m<m>(planes, n, pitch, vt, ro, grad2d, grad_planes, status, s)
   BETA_DISPATCH_M(n_lobes, CALL_B)

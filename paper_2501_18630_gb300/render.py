@@ -53,7 +53,8 @@ class Rasterizer:
         self.color = torch.empty(3 * self.total_pixels, dtype=torch.float32, device=dev)
         self.T_final = torch.empty(self.total_pixels, dtype=torch.float32, device=dev)
         self.n_contrib = torch.empty(self.total_pixels, dtype=torch.int32, device=dev)
-        self.grad2d = torch.empty(int(L.beta_grad2d_bytes(self.pitch, self.V)) // 4, dtype=torch.float32, device=dev)
+        # 2D-gradient accumulators: zero once here; beta_project_bwd re-clears them
+        self.grad2d = torch.zeros(int(L.beta_grad2d_bytes(self.pitch, self.V)) // 4, dtype=torch.float32, device=dev)
         self.loss = torch.zeros(self.V, dtype=torch.float32, device=dev)
         self.dL_dcolor = torch.empty_like(self.color)
         self.l1_ws = torch.empty(max(4, int(L.beta_l1_workspace_bytes(self.cams, self.V))), dtype=torch.uint8, device=dev)
@@ -111,14 +112,20 @@ class Rasterizer:
             _vp(self.l1_ws), self.l1_ws.numel(), _stream()))
         return self.loss, self.dL_dcolor
 
-    def raster_bwd(self, planes, dL_dcolor, grad_planes):
+    def raster_bwd(self, planes, dL_dcolor):
         prm = self.params(planes)
-        assert grad_planes.shape == planes.shape and grad_planes.is_contiguous()
         assert dL_dcolor.numel() == self.color.numel() and dL_dcolor.is_contiguous()
         _lib.check("beta_raster_bwd", self.L.beta_raster_bwd(
             ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
             _vp(self.pair_vals), _vp(self.ranges), _vp(self.T_final), _vp(self.n_contrib),
-            _vp(dL_dcolor), _vp(self.grad2d), _vp(grad_planes), _vp(self.status), _stream()))
+            _vp(dL_dcolor), _vp(self.grad2d), _vp(self.status), _stream()))
+
+    def project_bwd(self, planes, grad_planes):
+        prm = self.params(planes)
+        assert grad_planes.shape == planes.shape and grad_planes.is_contiguous()
+        _lib.check("beta_project_bwd", self.L.beta_project_bwd(
+            ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.grad2d),
+            _vp(grad_planes), _vp(self.status), _stream()))
 
     # -- composite calls ---------------------------------------------------
     def device_status(self):
@@ -145,7 +152,8 @@ class Rasterizer:
     def backward(self, planes, dL_dcolor, grad_planes=None):
         if grad_planes is None:
             grad_planes = torch.zeros_like(planes)
-        self.raster_bwd(planes, dL_dcolor, grad_planes)
+        self.raster_bwd(planes, dL_dcolor)
+        self.project_bwd(planes, grad_planes)
         return grad_planes
 
 
