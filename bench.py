@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the Beta-splatting rasterizer hot path on GB300.
+
+One step = forward + backward of every view of a batch through the whole hot
+path (project -> bin/sort -> raster fwd -> L1 loss -> raster bwd -> project
+bwd) on seeded synthetic inputs: 1M Betas (256 planar sheets, 3 spherical-Beta
+lobes), views of 1920x1080 on a ring of radius 4.  The batched path runs
+every view in the same launches; the plain per-view path (the baseline of the
+batched speedup) runs the same entry points one view at a time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--views V] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank renders its own
+views (weak scaling) and the parameter gradients are summed with one NCCL
+all-reduce per step.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/view and Mpixels/s at 1M Betas 1080p; batched vs per-view speedup"
+UNIT = "Mpixel/s"
+FWD_FLOPS_PER_EVAL = 24   # r^2 (11), 1 - r^2, beta lg2 + log2 o, min, T alpha, C += (6), T update
+BWD_FLOPS_PER_EVAL = 60   # recompute alpha, T recovery, dL/dalpha, 10 gradient terms
+FP32_LANES_PER_SM = 128
+STAGES = ["project", "bin_sort", "raster_fwd", "l1", "raster_bwd", "project_bwd"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--views", type=int, default=16)
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extras", action="store_true", help="skip per-view, e2e and CPU legs (profiling runs)")
+    ap.add_argument("--cpu-pixels", type=int, default=16384)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), float(p.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows]
+        out["samples"] = len(rows)
+        out["sm_mhz"] = statistics.median(sm)
+        out["sm_max_mhz"] = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for k, name in enumerate(names):
+            if any(r[5 + k].lower().startswith("active") for r in rows):
+                out["reasons"].append(name)
+        return out
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("beta_raster.cu", "beta_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2501_18630_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, launch_units: float):
+    """dram bytes per launch of `kernel` from the committed ncu summary, scaled
+    to this launch; None if absent or if the kernel source changed since."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+        e = d["kernels"][kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_unit"]) * launch_units
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_leg(args, cams, sc, pixels_per_step, steps, warmup):
+    import numpy as np
+
+    import oracle
+    from paper_2501_18630_gb300 import scenes
+    oracle.build()
+    cores = os.cpu_count() or 1
+    times = []
+    for s in range(warmup + steps):
+        cam = cams[s % len(cams)]
+        xs, ys = scenes.sample_pixels(cam, pixels_per_step, seed=1000 + s)
+        t0 = time.perf_counter()
+        oracle.render(sc.planes, sc.n, sc.n_lobes, cam, xs, ys, n_threads=cores)
+        dt = time.perf_counter() - t0
+        if s >= warmup:
+            times.append(dt)
+    total = sum(times)
+    value = pixels_per_step * len(times) / total / 1e6
+    return value, cores, total
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2501_18630_gb300 import scenes
+    sc = scenes.config_scene(3, n=args.n, n_views=args.views)
+    cams = scenes.ring_cameras(args.views, 4.0, 15.0, (args.width, args.height))
+    px = 1024
+    value, cores, total = oracle_leg(args, cams, sc, px, args.steps, args.warmup)
+    ms = total / args.steps * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.n} Betas (256 sheets, 3 SB lobes), {args.views} views "
+                               f"{args.width}x{args.height}; FP64 oracle forward on {px} sampled pixels per step",
+                   "n_betas": args.n, "views": args.views},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{px} seeded pixels of one view per step, forward only (the oracle has no backward)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_18630_gb300 import _lib, render, scenes
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    _lib.load()
+
+    V = args.views
+    sc = scenes.config_scene(3, n=args.n, n_views=V)
+    ring = scenes.ring_cameras(V * world, 4.0, 15.0, (args.width, args.height))
+    cams = ring[rank::world]
+    planes = torch.from_numpy(sc.planes).to(dev)
+    targets_np = scenes.target_images(cams, seed=77 + rank)
+    target = torch.from_numpy(np.concatenate([t.reshape(-1) for t in targets_np])).to(dev)
+    grad = torch.zeros_like(planes)
+
+    rast = render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, cams, device=dev)
+    rast.forward(planes, check_capacity=True)
+    _, K0 = rast.device_status()
+    rast._alloc_pairs(int(K0 * 1.1) + 65536)
+
+    def step(r=rast, g=grad):
+        r.project(planes)
+        r.bin_sort(planes)
+        r.raster_fwd(planes)
+        r.l1_loss(target)
+        r.raster_bwd(planes, r.dL_dcolor)
+        r.project_bwd(planes, g)
+        if world > 1:
+            dist.all_reduce(g)
+
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step()
+    st, K = rast.device_status()
+    if st != 0:
+        raise SystemExit(f"device status {st} after warm-up")
+
+    # ---- timed region: K batched steps -------------------------------------
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    ms_total = max_over_ranks(e0.elapsed_time(e1))
+    ms_step = ms_total / args.steps
+    clocks = clk.summary()
+    st, K = rast.device_status()
+    if st != 0:
+        raise SystemExit(f"device status {st} in the timed region")
+    pix_per_step = rast.total_pixels * world
+    value = pix_per_step / (ms_step * 1e-3) / 1e6
+
+    # ---- per-stage times (separate loop, events between the entry points) ---
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
+    stage_ms = {s: 0.0 for s in STAGES}
+    for _ in range(args.steps):
+        ev[0].record(stream)
+        rast.project(planes); ev[1].record(stream)
+        rast.bin_sort(planes); ev[2].record(stream)
+        rast.raster_fwd(planes); ev[3].record(stream)
+        rast.l1_loss(target); ev[4].record(stream)
+        rast.raster_bwd(planes, rast.dL_dcolor); ev[5].record(stream)
+        rast.project_bwd(planes, grad); ev[6].record(stream)
+        torch.cuda.synchronize()
+        for k, s in enumerate(STAGES):
+            stage_ms[s] += ev[k].elapsed_time(ev[k + 1]) / args.steps
+
+    # ---- roofline of the dominant kernel -----------------------------------
+    hbm_peak, sm_max_mhz, peak_src = peaks()
+    dom = max(stage_ms, key=stage_ms.get)
+    rec = rast.proj[: V * rast.pitch * 64].view(torch.float32).view(V, rast.pitch, 16)
+    keys = rast.proj[V * rast.pitch * 72: V * rast.pitch * 76].view(torch.int32).view(V, rast.pitch)
+    binned = keys != -1
+    area = math.pi / (rec[..., 4] * rec[..., 5]).clamp_min(1e-30)          # pi sqrt(det Sigma')
+    evals = float(torch.where(binned, area.clamp_max(args.width * args.height), torch.zeros_like(area)).sum().item())
+    alu_peak = 152 * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12      # TFLOP/s
+    n_planes = scenes.n_planes(sc.n_lobes)
+    if dom in ("raster_fwd", "raster_bwd"):
+        fl = FWD_FLOPS_PER_EVAL if dom == "raster_fwd" else BWD_FLOPS_PER_EVAL
+        achieved = evals * fl / (stage_ms[dom] * 1e-3) / 1e12
+        kname = "k_raster_fwd" if dom == "raster_fwd" else "k_raster_bwd"
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": ncu_traffic(kname, rast.total_pixels),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                "algorithmic": f"{fl} flop x {evals:.4g} (pixel, Beta) evaluations inside the support (ellipse areas)"}
+    else:
+        nrec = V * sc.n
+        bytes_alg = {"project": sc.n * n_planes * 4 + nrec * 76,
+                     "bin_sort": nrec * 8 * 4 + K * 8 * 3,
+                     "l1": rast.total_pixels * 3 * 4 * 3,
+                     "project_bwd": nrec * 40 * 2 + sc.n * n_planes * 8}.get(dom, 0)
+        achieved = bytes_alg / (stage_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None}
+    roof["peak_kind"] = f"{peak_src} (max SM clock {sm_max_mhz:.0f} MHz)" if roof["bound"] == "alu" else peak_src
+
+    extras = {}
+    if not args.no_extras:
+        # ---- plain per-view path (baseline of the batched speedup) ----------
+        singles = [render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, [c], device=dev) for c in cams]
+        gview = [torch.zeros_like(planes) for _ in cams]
+        tv = [target[3 * rast.pix_off[v]: 3 * rast.pix_off[v] + 3 * c.width * c.height] for v, c in enumerate(cams)]
+        for s in singles:
+            s.forward(planes, check_capacity=True)
+            _, k = s.device_status()
+            s._alloc_pairs(int(k * 1.1) + 65536)
+
+        def step_views():
+            for v, s in enumerate(singles):
+                s.project(planes)
+                s.bin_sort(planes)
+                s.raster_fwd(planes)
+                s.l1_loss(tv[v])
+                s.raster_bwd(planes, s.dL_dcolor)
+                s.project_bwd(planes, gview[v])
+
+        for _ in range(args.warmup):
+            step_views()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_views()
+        e1.record(stream)
+        barrier()
+        ms_views = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        extras["per_view_path"] = {"ms_per_step": ms_views, "ms_per_view": ms_views / V,
+                                   "value": pix_per_step / (ms_views * 1e-3) / 1e6}
+        extras["batched_speedup"] = ms_views / ms_step
+        del singles, gview
+
+        # ---- end to end through host buffers --------------------------------
+        h_planes = torch.from_numpy(sc.planes).pin_memory()
+        h_target = torch.from_numpy(np.concatenate([t.reshape(-1) for t in targets_np])).pin_memory()
+        h_grad = torch.empty(planes.shape, dtype=torch.float32).pin_memory()
+        h_loss = torch.empty(V, dtype=torch.float32).pin_memory()
+
+        def step_e2e():
+            planes.copy_(h_planes, non_blocking=True)
+            target.copy_(h_target, non_blocking=True)
+            step()
+            h_grad.copy_(grad, non_blocking=True)
+            h_loss.copy_(rast.loss, non_blocking=True)
+
+        for _ in range(args.warmup):
+            step_e2e()
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_e2e()
+        e1.record(stream)
+        barrier()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        extras["e2e"] = {"value": pix_per_step / (ms_e2e * 1e-3) / 1e6, "unit": UNIT,
+                         "h2d_bytes_per_step": (h_planes.numel() + h_target.numel()) * 4 * world,
+                         "d2h_bytes_per_step": (h_grad.numel() + h_loss.numel()) * 4 * world,
+                         "ms_per_step": ms_e2e}
+
+        # ---- the oracle on the host cores (bounded sample) -------------------
+        if rank == 0 and world == 1:
+            v_cpu, cores, tot = oracle_leg(args, cams[:1], sc, args.cpu_pixels, 1, 0)
+            extras["cpu_baseline"] = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                      "sample": f"{args.cpu_pixels} seeded pixels of view 0 of the same "
+                                                f"workload, forward only (FP64, every Beta per pixel), {tot:.1f} s"}
+
+    # kernel launches of ours inside the timed region
+    np_t = math.ceil(math.ceil(math.log2(max(rast.total_tiles, 2))) / 8)
+    per_step = 1 + (1 + 1 + 4 + 3 + (1 + np_t if np_t > 0 else 0) + 1) + 1 + 2 + 1 + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.n} Betas (256 planar sheets, 3 SB lobes), {V} views {args.width}x{args.height} "
+                               f"per GPU, fwd+bwd with per-view L1 loss, batched launches",
+                   "n_betas": args.n, "views_per_gpu": V, "resolution": f"{args.width}x{args.height}",
+                   "pairs_per_step": K, "l2": f"inputs larger than L2: {args.n * n_planes * 4 / 1e6:.0f} MB params + "
+                                               f"{V * sc.pitch * 76 / 1e6:.0f} MB records per step",
+                   "parallelism": f"dp{world} over views"},
+        "ms_per_view": ms_step / V,
+        "stage_ms": stage_ms,
+        "roofline": roof,
+        "clocks": clocks,
+        "gpu_launches": per_step * args.steps,
+        "kernel_source": kernel_source_hash(),
+    }
+    line.update({k: v for k, v in extras.items()})
+    if "cpu_baseline" not in line and world == 1 and not args.no_extras:
+        line["cpu_baseline"] = None
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
