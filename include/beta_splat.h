@@ -150,6 +150,37 @@ int beta_bin_sort(const beta_params* prm, const beta_camera* cams, int32_t n_vie
                   int64_t pair_capacity, uint32_t* tile_ranges, int64_t* d_pair_count,
                   int32_t* d_status, void* ws, size_t ws_bytes, beta_stream_t stream);
 
+/* Size of the library's own device scratch array used by
+ * beta_bin_sort_static (32 MiB). */
+#define BETA_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* beta_bin_sort without a caller workspace.  The paper has no counterpart:
+ * this is a deployment convenience.  Some callers cannot allocate device
+ * memory at all -- a plugin whose host application owns every device
+ * allocation, a real-time loop where cudaMalloc's implicit device
+ * synchronisation is not allowed, or a deployment that must reserve all
+ * memory when the library is loaded.  They call this variant instead: it is
+ * beta_bin_sort with its workspace taken from a file-scope __device__ array
+ * of BETA_STATIC_SCRATCH_BYTES inside the library (every GPU that loads the
+ * library holds that array until the process exits).  The caller still
+ * passes the inputs and outputs, and the call allocates nothing.
+ *   - Problems whose workspace (beta_binsort_workspace_bytes) exceeds
+ *     BETA_STATIC_SCRATCH_BYTES are rejected with BETA_ERR_WORKSPACE before
+ *     anything is launched.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one array, and it keeps what the last
+ *     call left in it (the call clears every part that must start at zero).
+ *     Calls whose kernels overlap on the GPU (different streams, or
+ *     different host threads without ordering) race on the array: order them
+ *     on one stream.
+ * Arguments, outputs and status codes are those of beta_bin_sort. */
+int beta_bin_sort_static(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                         const beta_opts* opt, const void* proj, uint32_t* pair_vals,
+                         int64_t pair_capacity, uint32_t* tile_ranges, int64_t* d_pair_count,
+                         int32_t* d_status, beta_stream_t stream);
+
 /* Step 3 (Eq. C): front-to-back compositing of every tile's sorted list.
  *   color     [3 x total_pixels] out: C + T_final * bg (planar per view)
  *   T_final   [total_pixels] out: final transmittance

@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "beta_internal.cuh"
 #include "beta_splat.h"
 
@@ -92,6 +94,29 @@ RenderOpts render_opts(const beta_opts* o) {
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? BETA_OK : BETA_ERR_CUDA; }
+
+// Device scratch of beta_bin_sort_static: a fixed array inside the library,
+// so callers that cannot allocate need not provide a workspace.
+static __device__ __align__(256) unsigned char g_binsort_scratch[BETA_STATIC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_binsort_scratch on the current device (looked up once
+// per device; the host-side symbol itself is not a device address).
+int static_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BETA_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_binsort_scratch) != cudaSuccess || !p) return BETA_ERR_CUDA;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return BETA_OK;
+}
 
 }  // namespace
 
@@ -192,6 +217,27 @@ int beta_bin_sort(const beta_params* prm, const beta_camera* cams, int32_t n_vie
   if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
   size_t need = binsort_ws_bytes((int64_t)prm->pitch * n_views, pair_capacity, vt.total_tiles);
   if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u) != 0) return BETA_ERR_WORKSPACE;
+  ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
+  return cuda_status(launch_bin_sort(vt, prm->pitch, pb, pair_vals, pair_capacity, tile_ranges,
+                                     d_pair_count, d_status, ws, (cudaStream_t)stream));
+}
+
+int beta_bin_sort_static(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                         const beta_opts* opt, const void* proj, uint32_t* pair_vals,
+                         int64_t pair_capacity, uint32_t* tile_ranges, int64_t* d_pair_count,
+                         int32_t* d_status, beta_stream_t stream) {
+  if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !d_pair_count || !d_status)
+    return BETA_ERR_ARG;
+  if (pair_capacity < 0 || pair_capacity > 0x7fffffffll || (pair_capacity > 0 && !pair_vals))
+    return BETA_ERR_ARG;
+  int e = check_opts(opt);
+  if (e != BETA_OK) return e;
+  ViewTable vt;
+  if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  size_t need = binsort_ws_bytes((int64_t)prm->pitch * n_views, pair_capacity, vt.total_tiles);
+  if (need > (size_t)BETA_STATIC_SCRATCH_BYTES) return BETA_ERR_WORKSPACE;
+  void* ws = nullptr;
+  if ((e = static_scratch(&ws)) != BETA_OK) return e;
   ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
   return cuda_status(launch_bin_sort(vt, prm->pitch, pb, pair_vals, pair_capacity, tile_ranges,
                                      d_pair_count, d_status, ws, (cudaStream_t)stream));
