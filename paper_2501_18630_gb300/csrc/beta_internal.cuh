@@ -17,7 +17,7 @@ constexpr int kRecordF4 = 4;      // raster record: 4 x float4 = 64 bytes
 //   f4[0] = (mx_int, my_int, off_x, off_y)  centre mu' = mx_int + 0.5 - off_x
 //   f4[1] = (p, q1, q2, beta)               whitening: u = p dx, v = q2 dx + q1 dy, r^2 = u^2 + v^2
 //   f4[2] = (log2 o, c_r, c_g, c_b)
-//   f4[3] = (ex, ey, o, 0)                  conservative half extents of the support box
+//   f4[3] = (ex, ey, 1/o, 0)                conservative half extents of the support box, 1/opacity
 // Pixel (x, y) has dx = (x - mx_int) + off_x, which is exact up to one rounding.
 
 struct ViewDev {
@@ -97,31 +97,27 @@ __device__ __forceinline__ float rn_dot3(float a0, float b0, float a1, float b1,
   return __fadd_rn(s, __fmul_rn(a2, b2));
 }
 
-struct Geo {
-  // inputs (fp32)
+// View-independent part of the rule chain: scales, normalised quaternion and
+// its rotation matrix.
+struct PrimGeo {
   float mu[3], s[3], q[4];   // q normalised
   float Rq[9];               // rotation of q
+  float qn;                  // |q|
+};
+
+// Per-view part of the rule chain.
+struct ViewGeo {
   float A[9];                // W Rq
   float tc[3];               // camera-space centre (rule D)
   float iz, j00, j11, j02, j12;
   float M0[3], M1[3];        // M = J W Rq S (2 x 3)
   float sxx, syy;            // diagonal of Sigma' (blur included)
-  float qn;                  // |q|
 };
 
-// Rule chain.  Returns false when the primitive is culled for this view
-// (non-finite handled by the caller).  On success fills g, rect and key.
-__device__ __forceinline__ bool rule_chain(const float* p, const ViewDev& V, float blur,
-                                           Geo& g, int rect[4], uint32_t& key) {
+// Rule chain, view-independent part.  Returns false if the primitive is
+// culled in every view (log-scale out of [-80, 80] or a zero quaternion).
+__device__ __forceinline__ bool rule_prim(const float* p, PrimGeo& g) {
   g.mu[0] = p[0]; g.mu[1] = p[1]; g.mu[2] = p[2];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    float s = __fadd_rn(__fmul_rn(V.R[r * 3 + 0], g.mu[0]), __fmul_rn(V.R[r * 3 + 1], g.mu[1]));
-    s = __fadd_rn(s, __fmul_rn(V.R[r * 3 + 2], g.mu[2]));
-    g.tc[r] = __fadd_rn(s, V.t[r]);
-  }
-  key = __float_as_uint(g.tc[2]);
-  if (!(g.tc[2] > V.near_plane)) return false;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     float l = p[3 + k];
@@ -151,12 +147,33 @@ __device__ __forceinline__ bool rule_chain(const float* p, const ViewDev& V, flo
   g.Rq[6] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
   g.Rq[7] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
   g.Rq[8] = __fsub_rn(1.0f, __fmul_rn(2.0f, __fadd_rn(xx, yy)));
+  return true;
+}
+
+// Camera-space centre and depth key (rule D).  Returns false at or behind
+// the near plane.
+__device__ __forceinline__ bool rule_depth(const PrimGeo& pg, const ViewDev& V, ViewGeo& g,
+                                           uint32_t& key) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    float s = __fadd_rn(__fmul_rn(V.R[r * 3 + 0], pg.mu[0]), __fmul_rn(V.R[r * 3 + 1], pg.mu[1]));
+    s = __fadd_rn(s, __fmul_rn(V.R[r * 3 + 2], pg.mu[2]));
+    g.tc[r] = __fadd_rn(s, V.t[r]);
+  }
+  key = __float_as_uint(g.tc[2]);
+  return g.tc[2] > V.near_plane;
+}
+
+// Rule chain, per-view part after rule_depth: J, M, diagonal of Sigma' and
+// the tile rectangle.  Returns false if the rectangle is empty.
+__device__ __forceinline__ bool rule_view(const PrimGeo& pg, const ViewDev& V, float blur,
+                                          ViewGeo& g, int rect[4]) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      g.A[r * 3 + c] = rn_dot3(V.R[r * 3 + 0], g.Rq[0 * 3 + c], V.R[r * 3 + 1], g.Rq[1 * 3 + c],
-                               V.R[r * 3 + 2], g.Rq[2 * 3 + c]);
+      g.A[r * 3 + c] = rn_dot3(V.R[r * 3 + 0], pg.Rq[0 * 3 + c], V.R[r * 3 + 1], pg.Rq[1 * 3 + c],
+                               V.R[r * 3 + 2], pg.Rq[2 * 3 + c]);
   g.iz = __fdiv_rn(1.0f, g.tc[2]);
   g.j00 = __fmul_rn(V.fx, g.iz);
   g.j11 = __fmul_rn(V.fy, g.iz);
@@ -164,8 +181,8 @@ __device__ __forceinline__ bool rule_chain(const float* p, const ViewDev& V, flo
   g.j12 = -__fmul_rn(__fmul_rn(g.j11, g.tc[1]), g.iz);
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    g.M0[c] = __fmul_rn(__fadd_rn(__fmul_rn(g.j00, g.A[0 * 3 + c]), __fmul_rn(g.j02, g.A[2 * 3 + c])), g.s[c]);
-    g.M1[c] = __fmul_rn(__fadd_rn(__fmul_rn(g.j11, g.A[1 * 3 + c]), __fmul_rn(g.j12, g.A[2 * 3 + c])), g.s[c]);
+    g.M0[c] = __fmul_rn(__fadd_rn(__fmul_rn(g.j00, g.A[0 * 3 + c]), __fmul_rn(g.j02, g.A[2 * 3 + c])), pg.s[c]);
+    g.M1[c] = __fmul_rn(__fadd_rn(__fmul_rn(g.j11, g.A[1 * 3 + c]), __fmul_rn(g.j12, g.A[2 * 3 + c])), pg.s[c]);
   }
   float sxx = __fmul_rn(g.M0[0], g.M0[0]);
   sxx = __fadd_rn(sxx, __fmul_rn(g.M0[1], g.M0[1]));

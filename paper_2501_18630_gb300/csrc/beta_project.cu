@@ -56,14 +56,42 @@ __device__ __forceinline__ void load_params(const float* __restrict__ planes, in
   }
 }
 
+// View-independent per-primitive quantities of the forward.
 template <int M>
-__device__ __forceinline__ void sb_colour(const float* p, const ViewDev& V, int mode, float c[3]) {
-  c[0] = c[1] = c[2] = 0.0f;
-  if (mode != 2) {
-    c[0] = p[12];
-    c[1] = p[13];
-    c[2] = p[14];
+struct PrimAttr {
+  float o, log2o, beta;
+  float c0[3];
+  float lobe_dir[M > 0 ? M : 1][3];
+  float lobe_beta[M > 0 ? M : 1];
+};
+
+template <int M>
+__device__ __forceinline__ void prim_attr(const float* p, int mode, PrimAttr<M>& a) {
+  a.o = sigmoidf(p[10]);
+  a.log2o = log2_sigmoid(p[10]);
+  a.beta = 4.0f * expf(p[11]);
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) a.c0[ch] = (mode != 2) ? p[12 + ch] : 0.0f;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const float* L = p + 15 + 6 * m;
+    float st, ct, sp, cp;
+    sincosf(L[0], &st, &ct);
+    sincosf(L[1], &sp, &cp);
+    a.lobe_dir[m][0] = st * cp;
+    a.lobe_dir[m][1] = st * sp;
+    a.lobe_dir[m][2] = ct;
+    a.lobe_beta[m] = 4.0f * expf(L[2]);
   }
+}
+
+// spherical-Beta colour for view direction V = normalize(mu - campos)
+template <int M>
+__device__ __forceinline__ void sb_colour(const float* p, const PrimAttr<M>& a, const ViewDev& V,
+                                          int mode, float c[3]) {
+  c[0] = a.c0[0];
+  c[1] = a.c0[1];
+  c[2] = a.c0[2];
   if (M > 0 && mode != 1) {
     float vx = p[0] - V.campos[0], vy = p[1] - V.campos[1], vz = p[2] - V.campos[2];
     float inv = rsqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
@@ -73,12 +101,9 @@ __device__ __forceinline__ void sb_colour(const float* p, const ViewDev& V, int 
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       const float* L = p + 15 + 6 * m;
-      float st, ct, sp, cp;
-      sincosf(L[0], &st, &ct);
-      sincosf(L[1], &sp, &cp);
-      float dot = st * cp * vx + st * sp * vy + ct * vz;
+      float dot = a.lobe_dir[m][0] * vx + a.lobe_dir[m][1] * vy + a.lobe_dir[m][2] * vz;
       if (dot > 0.0f) {
-        float w = exp2f(4.0f * expf(L[2]) * log2f(dot));
+        float w = exp2f(a.lobe_beta[m] * log2f(dot));
         c[0] = fmaf(w, L[3], c[0]);
         c[1] = fmaf(w, L[4], c[1]);
         c[2] = fmaf(w, L[5], c[2]);
@@ -98,17 +123,21 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
   bool ok = false;
   if (i < n) load_params<M>(planes, pitch, i, p, ok);
   if (ok) ok = (p[11] >= ro.b_lo) && (p[11] < ro.b_hi);
+  PrimGeo pg;
+  if (ok) ok = rule_prim(p, pg);
+  PrimAttr<M> at;
+  if (ok) prim_attr<M>(p, ro.color_mode, at);
   for (int v = 0; v < vt.n_views; ++v) {
     const ViewDev& V = vt.v[v];
     const size_t r = (size_t)v * pitch + i;
-    Geo g;
+    ViewGeo g;
     int rc[4];
     uint32_t kk = 0xffffffffu;
-    bool bin = ok && rule_chain(p, V, ro.blur_eps, g, rc, kk);
+    bool bin = ok && rule_depth(pg, V, g, kk) && rule_view(pg, V, ro.blur_eps, g, rc);
     float4 o0, o1, o2, o3;
     if (bin) {
       // projected centre in double-float
-      dd tx = cam_coord_dd(V, 0, g.mu), ty = cam_coord_dd(V, 1, g.mu), tz = cam_coord_dd(V, 2, g.mu);
+      dd tx = cam_coord_dd(V, 0, pg.mu), ty = cam_coord_dd(V, 1, pg.mu), tz = cam_coord_dd(V, 2, pg.mu);
       dd mx = dd_add_f(dd_mul_f(dd_div(tx, tz), V.fx), V.cx);
       dd my = dd_add_f(dd_mul_f(dd_div(ty, tz), V.fy), V.cy);
       float ix = floorf(mx.hi), iy = floorf(my.hi);
@@ -133,15 +162,14 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
         float pp = 1.0f / sa;
         float q1 = sa / sd;
         float q2 = -(b * pp) / sd;
-        float beta = 4.0f * expf(p[11]);
         float col[3];
-        sb_colour<M>(p, V, ro.color_mode, col);
+        sb_colour<M>(p, at, V, ro.color_mode, col);
         const float INFL = 1.000244140625f, PAD = 0.015625f;
         float ex = sqrtf(g.sxx) * INFL + PAD, ey = sqrtf(g.syy) * INFL + PAD;
         o0 = make_float4(ix, iy, 0.5f - fx, 0.5f - fy);
-        o1 = make_float4(pp, q1, q2, beta);
-        o2 = make_float4(log2_sigmoid(p[10]), col[0], col[1], col[2]);
-        o3 = make_float4(ex, ey, sigmoidf(p[10]), 0.0f);
+        o1 = make_float4(pp, q1, q2, at.beta);
+        o2 = make_float4(at.log2o, col[0], col[1], col[2]);
+        o3 = make_float4(ex, ey, 1.0f + expf(-p[10]), 0.0f);   // 1 / o
       }
     }
     if (bin) {
@@ -160,7 +188,9 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
 
 // ---------------------------------------------------------------------------
 // backward: 2D gradients (d mu', d Sigma' (a, b, c), d o, d beta, d colour)
-// of every view -> gradients of the raw parameters.
+// of every view -> gradients of the raw parameters.  Gradients w.r.t. the
+// rotation matrix, the scales and the lobe directions are summed over views
+// first and taken through the view-independent maps once.
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ planes, int n,
@@ -171,6 +201,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   constexpr int NP = 15 + 6 * M;
+  constexpr int MM = M > 0 ? M : 1;
   float gp[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) gp[k] = 0.0f;
@@ -179,9 +210,19 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
   load_params<M>(planes, pitch, i, p, ok);
   if (ok) ok = (p[11] >= ro.b_lo) && (p[11] < ro.b_hi);
   if (*status != 0) ok = false;
+  PrimGeo pg;
+  if (ok) ok = rule_prim(p, pg);
   if (ok) {
-    const float o = sigmoidf(p[10]);
-    const float beta = 4.0f * expf(p[11]);
+    PrimAttr<M> at;
+    prim_attr<M>(p, ro.color_mode, at);
+    float dR[9], ds[3], dRm[MM][3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dR[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ds[k] = 0.0f;
+#pragma unroll
+    for (int m = 0; m < MM; ++m) dRm[m][0] = dRm[m][1] = dRm[m][2] = 0.0f;
+    float go = 0.0f, gbeta = 0.0f;
     for (int v = 0; v < vt.n_views; ++v) {
       const ViewDev& V = vt.v[v];
       float* g2 = grad2d + ((size_t)v * pitch + i) * kGrad2d;
@@ -196,10 +237,10 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
       // leave the accumulator zeroed for the next backward
 #pragma unroll
       for (int k = 0; k < kGrad2d; ++k) g2[k] = 0.0f;
-      Geo g;
+      ViewGeo g;
       int rc[4];
       uint32_t kk;
-      if (!rule_chain(p, V, ro.blur_eps, g, rc, kk)) continue;
+      if (!rule_depth(pg, V, g, kk) || !rule_view(pg, V, ro.blur_eps, g, rc)) continue;
       const float gmx = G[0], gmy = G[1], ga = G[2], gb = G[3], gc = G[4];
       // Sigma' = M M^T: dM0 = 2 ga M0 + gb M1, dM1 = gb M0 + 2 gc M1
       float dM0[3], dM1[3];
@@ -215,39 +256,22 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
       for (int k = 0; k < 3; ++k) {
         float u0 = g.j00 * g.A[0 * 3 + k] + g.j02 * g.A[2 * 3 + k];
         float u1 = g.j11 * g.A[1 * 3 + k] + g.j12 * g.A[2 * 3 + k];
-        float ds = dM0[k] * u0 + dM1[k] * u1;
-        gp[3 + k] += ds * g.s[k];                      // d log-scale
-        dA[0 * 3 + k] = dM0[k] * g.j00 * g.s[k];
-        dA[1 * 3 + k] = dM1[k] * g.j11 * g.s[k];
-        dA[2 * 3 + k] = (dM0[k] * g.j02 + dM1[k] * g.j12) * g.s[k];
-        dj00 += dM0[k] * g.A[0 * 3 + k] * g.s[k];
-        dj02 += dM0[k] * g.A[2 * 3 + k] * g.s[k];
-        dj11 += dM1[k] * g.A[1 * 3 + k] * g.s[k];
-        dj12 += dM1[k] * g.A[2 * 3 + k] * g.s[k];
+        ds[k] += dM0[k] * u0 + dM1[k] * u1;
+        dA[0 * 3 + k] = dM0[k] * g.j00 * pg.s[k];
+        dA[1 * 3 + k] = dM1[k] * g.j11 * pg.s[k];
+        dA[2 * 3 + k] = (dM0[k] * g.j02 + dM1[k] * g.j12) * pg.s[k];
+        dj00 += dM0[k] * g.A[0 * 3 + k] * pg.s[k];
+        dj02 += dM0[k] * g.A[2 * 3 + k] * pg.s[k];
+        dj11 += dM1[k] * g.A[1 * 3 + k] * pg.s[k];
+        dj12 += dM1[k] * g.A[2 * 3 + k] * pg.s[k];
       }
-      // A = W Rq  ->  dRq = W^T dA
-      float dR[9];
+      // A = W Rq  ->  dRq += W^T dA
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          dR[a * 3 + c] = V.R[0 * 3 + a] * dA[0 * 3 + c] + V.R[1 * 3 + a] * dA[1 * 3 + c] +
-                          V.R[2 * 3 + a] * dA[2 * 3 + c];
-      // Rq(q_hat) -> d q_hat
-      const float w = g.q[0], x = g.q[1], y = g.q[2], z = g.q[3];
-      float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
-      float dx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
-                        w * dR[7] - 2.f * x * dR[8]);
-      float dy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
-                        z * dR[7] - 2.f * y * dR[8]);
-      float dz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] +
-                        y * dR[5] + x * dR[6] + y * dR[7]);
-      float qd = w * dw + x * dx + y * dy + z * dz;
-      float iq = 1.0f / g.qn;
-      gp[6] += (dw - w * qd) * iq;
-      gp[7] += (dx - x * qd) * iq;
-      gp[8] += (dy - y * qd) * iq;
-      gp[9] += (dz - z * qd) * iq;
+          dR[a * 3 + c] += V.R[0 * 3 + a] * dA[0 * 3 + c] + V.R[1 * 3 + a] * dA[1 * 3 + c] +
+                           V.R[2 * 3 + a] * dA[2 * 3 + c];
       // J(t) and mu'(t)
       const float tx = g.tc[0], ty = g.tc[1], iz = g.iz, iz2 = iz * iz, iz3 = iz2 * iz;
       float dtx = dj02 * (-V.fx * iz2) + gmx * V.fx * iz;
@@ -258,9 +282,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
       gp[0] += V.R[0] * dtx + V.R[3] * dty + V.R[6] * dtz;
       gp[1] += V.R[1] * dtx + V.R[4] * dty + V.R[7] * dtz;
       gp[2] += V.R[2] * dtx + V.R[5] * dty + V.R[8] * dtz;
-      // opacity and shape
-      gp[10] += G[5] * o * (1.0f - o);
-      gp[11] += G[6] * beta;
+      go += G[5];
+      gbeta += G[6];
       // colour
       const float gr = G[7], gg = G[8], gbl = G[9];
       if (ro.color_mode != 2) {
@@ -280,13 +303,10 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
         for (int m = 0; m < M; ++m) {
           const float* L = p + 15 + 6 * m;
           float* dL = gp + 15 + 6 * m;
-          float st, ct, sp, cp;
-          sincosf(L[0], &st, &ct);
-          sincosf(L[1], &sp, &cp);
-          float rx = st * cp, ry = st * sp, rz = ct;
+          const float rx = at.lobe_dir[m][0], ry = at.lobe_dir[m][1], rz = at.lobe_dir[m][2];
           float dot = rx * vx + ry * vy + rz * vz;
           if (dot > 0.0f) {
-            float bm = 4.0f * expf(L[2]);
+            float bm = at.lobe_beta[m];
             float lw = log2f(dot);
             float wgt = exp2f(bm * lw);
             dL[3] += wgt * gr;
@@ -295,9 +315,9 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
             float gw = gr * L[3] + gg * L[4] + gbl * L[5];
             dL[2] += gw * wgt * (lw * kLn2) * bm;
             float ddot = gw * bm * exp2f((bm - 1.0f) * lw);
-            float drx = ddot * vx, dry = ddot * vy, drz = ddot * vz;
-            dL[0] += drx * ct * cp + dry * ct * sp - drz * st;
-            dL[1] += -drx * st * sp + dry * st * cp;
+            dRm[m][0] += ddot * vx;
+            dRm[m][1] += ddot * vy;
+            dRm[m][2] += ddot * vz;
             dvx += ddot * rx;
             dvy += ddot * ry;
             dvz += ddot * rz;
@@ -308,6 +328,37 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
         gp[1] += (dvy - vy * vd) * il;
         gp[2] += (dvz - vz * vd) * il;
       }
+    }
+    // scales: s = exp(log-scale)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) gp[3 + k] = ds[k] * pg.s[k];
+    // Rq(q_hat) -> d q_hat -> d q
+    const float w = pg.q[0], x = pg.q[1], y = pg.q[2], z = pg.q[3];
+    float dw = 2.f * (-z * dR[1] + y * dR[2] + z * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+    float dx = 2.f * (y * dR[1] + z * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + z * dR[6] +
+                      w * dR[7] - 2.f * x * dR[8]);
+    float dy = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + z * dR[5] - w * dR[6] +
+                      z * dR[7] - 2.f * y * dR[8]);
+    float dz = 2.f * (-2.f * z * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * z * dR[4] +
+                      y * dR[5] + x * dR[6] + y * dR[7]);
+    float qd = w * dw + x * dx + y * dy + z * dz;
+    float iq = 1.0f / pg.qn;
+    gp[6] = (dw - w * qd) * iq;
+    gp[7] = (dx - x * qd) * iq;
+    gp[8] = (dy - y * qd) * iq;
+    gp[9] = (dz - z * qd) * iq;
+    // opacity logit and shape
+    gp[10] = go * at.o * (1.0f - at.o);
+    gp[11] = gbeta * at.beta;
+    // lobe directions R = (sin t cos p, sin t sin p, cos t)
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const float* L = p + 15 + 6 * m;
+      float st, ct, sp, cp;
+      sincosf(L[0], &st, &ct);
+      sincosf(L[1], &sp, &cp);
+      gp[15 + 6 * m + 0] = dRm[m][0] * ct * cp + dRm[m][1] * ct * sp - dRm[m][2] * st;
+      gp[15 + 6 * m + 1] = -dRm[m][0] * st * sp + dRm[m][1] * st * cp;
     }
   }
 #pragma unroll

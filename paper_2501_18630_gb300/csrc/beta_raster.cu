@@ -32,26 +32,48 @@ namespace beta {
 
 namespace {
 
-__device__ __forceinline__ uint8_t warp_mask(float4 f0, float4 f3, float tx0f, float ty0f) {
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// r^2 at offset (dx, dy) from the centre, for the whitening (p, q1, q2)
+__device__ __forceinline__ float r2_at(float p, float q1, float q2, float dx, float dy) {
+  const float u = p * dx;
+  const float v = fmaf(q2, dx, q1 * dy);
+  return fmaf(u, u, v * v);
+}
+
+// Bit w of the result is set when the support ellipse of a record can cover a
+// pixel centre of warp w's 8x4 block.  Exact up to a 1% margin on r^2: the
+// minimum of the convex r^2 over the block's rectangle of pixel centres is at
+// the ellipse centre if it lies inside, else on an edge, where it is the
+// clamped 1D minimiser.
+__device__ __forceinline__ uint8_t warp_mask(float4 f0, float4 f1, float4 f3, float tx0f, float ty0f) {
   // centre relative to the tile origin, in pixel-index coordinates
-  float rx = (f0.x - tx0f) - f0.z;
-  float ry = (f0.y - ty0f) - f0.w;
-  float ex = f3.x, ey = f3.y;
-  uint32_t xm = 0, ym = 0;
-#pragma unroll
-  for (int cb = 0; cb < 2; ++cb) {
-    float bx = 8.0f * cb;
-    if (rx + ex >= bx && rx - ex <= bx + 7.0f) xm |= 1u << cb;
-  }
-#pragma unroll
-  for (int rb = 0; rb < 4; ++rb) {
-    float by = 4.0f * rb;
-    if (ry + ey >= by && ry - ey <= by + 3.0f) ym |= 1u << rb;
-  }
+  const float rx = (f0.x - tx0f) - f0.z;
+  const float ry = (f0.y - ty0f) - f0.w;
+  const float ex = f3.x, ey = f3.y;
+  const float p = f1.x, q1 = f1.y, q2 = f1.z;
+  const float kv = -q2 / q1;                        // dy minimising r^2 at fixed dx, per unit dx
+  const float kh = -(q1 * q2) / fmaf(p, p, q2 * q2);  // dx minimising r^2 at fixed dy, per unit dy
   uint32_t m = 0;
 #pragma unroll
-  for (int w = 0; w < 8; ++w)
-    if (((xm >> (w & 1)) & 1u) && ((ym >> (w >> 1)) & 1u)) m |= 1u << w;
+  for (int w = 0; w < 8; ++w) {
+    const float bx = 8.0f * (w & 1), by = 4.0f * (w >> 1);
+    const float x0 = bx - rx, x1 = bx + 7.0f - rx, y0 = by - ry, y1 = by + 3.0f - ry;
+    if (x1 < -ex || x0 > ex || y1 < -ey || y0 > ey) continue;   // bounding box misses the block
+    bool hit = (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f);
+    if (!hit) {
+      float r = r2_at(p, q1, q2, x0, fminf(fmaxf(kv * x0, y0), y1));
+      r = fminf(r, r2_at(p, q1, q2, x1, fminf(fmaxf(kv * x1, y0), y1)));
+      r = fminf(r, r2_at(p, q1, q2, fminf(fmaxf(kh * y0, x0), x1), y0));
+      r = fminf(r, r2_at(p, q1, q2, fminf(fmaxf(kh * y1, x0), x1), y1));
+      hit = r < 1.01f;
+    }
+    if (hit) m |= 1u << w;
+  }
   return (uint8_t)m;
 }
 
@@ -90,14 +112,14 @@ __global__ void __launch_bounds__(kThreads) k_raster_fwd(ViewTable vt, RenderOpt
     const uint32_t j = base + tid;
     if (j < end) {
       const uint32_t r = vals[j];
-      float4 f0 = rec[(size_t)r * 4 + 0];
-      float4 f1 = rec[(size_t)r * 4 + 1];
-      float4 f2 = rec[(size_t)r * 4 + 2];
-      float4 f3 = rec[(size_t)r * 4 + 3];
+      const float4 f0 = rec[(size_t)r * 4 + 0];
+      const float4 f1 = rec[(size_t)r * 4 + 1];
+      const float4 f2 = rec[(size_t)r * 4 + 2];
+      const float4 f3 = rec[(size_t)r * 4 + 3];
       s_rec[tid][0] = f0;
       s_rec[tid][1] = f1;
       s_rec[tid][2] = f2;
-      s_mask[tid] = warp_mask(f0, f3, tx0f, ty0f);
+      s_mask[tid] = warp_mask(f0, f1, f3, tx0f, ty0f);
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kThreads, end - base);
@@ -145,6 +167,53 @@ __global__ void __launch_bounds__(kThreads) k_raster_fwd(ViewTable vt, RenderOpt
   }
 }
 
+// Sum of ten per-lane values over the warp, scattered: on return lane L holds
+// the warp total of field warp_sum10_field(L) (lanes with bit 0 set, and for
+// fields 2..4 / 7..9 also lanes with bit 1 set, hold duplicates).  12 shuffles.
+__device__ __forceinline__ float warp_sum10(const float v[10], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  float a[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const float send = b4 ? v[j] : v[j + 5];
+    const float keep = b4 ? v[j + 5] : v[j];
+    a[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float b[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float hi = j < 2 ? a[j + 3] : 0.0f;
+    const float send = b3 ? a[j] : hi;
+    const float keep = b3 ? hi : a[j];
+    b[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const float send0 = b3 ? (b2 ? b[0] : b[1]) : (b2 ? b[0] : b[2]);
+  const float keep0 = b3 ? (b2 ? b[1] : b[0]) : (b2 ? b[2] : b[0]);
+  const float c0 = keep0 + __shfl_xor_sync(0xffffffffu, send0, 4);
+  const float send1 = (!b3 && b2) ? b[1] : 0.0f;
+  const float keep1 = (!b3 && !b2) ? b[1] : 0.0f;
+  const float c1 = keep1 + __shfl_xor_sync(0xffffffffu, send1, 4);
+  const bool two = !b3 && !b2;
+  const float sendd = two ? (b1 ? c0 : c1) : c0;
+  const float keepd = two ? (b1 ? c1 : c0) : c0;
+  float d = keepd + __shfl_xor_sync(0xffffffffu, sendd, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
+}
+
+// field held by `lane` after warp_sum10, or -1 for a duplicate holder
+__device__ __forceinline__ int warp_sum10_field(int lane) {
+  if (lane & 1) return -1;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+  int sub;
+  if (!b3 && !b2) sub = b1 ? 1 : 0;
+  else {
+    if (b1) return -1;
+    sub = b3 ? (b2 ? 4 : 3) : 2;
+  }
+  return (b4 ? 5 : 0) + sub;
+}
+
 __global__ void __launch_bounds__(kThreads) k_raster_bwd(ViewTable vt, RenderOpts ro,
                                                          const float4* __restrict__ rec,
                                                          const uint32_t* __restrict__ vals,
@@ -172,6 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_raster_bwd(ViewTable vt, RenderOpt
   const float tx0f = (float)(tx * 16), ty0f = (float)(ty * 16);
   const uint32_t start = ranges[g];
   const float amax = ro.alpha_max;
+  const int my_field = warp_sum10_field(lane);
 
   float T = 1.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, GS = 0.0f;
   uint32_t nl = 0;
@@ -199,15 +269,15 @@ __global__ void __launch_bounds__(kThreads) k_raster_bwd(ViewTable vt, RenderOpt
     __syncthreads();
     if (tid < cnt) {
       const uint32_t r = vals[start + lo + tid];
-      float4 f0 = rec[(size_t)r * 4 + 0];
-      float4 f1 = rec[(size_t)r * 4 + 1];
-      float4 f2 = rec[(size_t)r * 4 + 2];
-      float4 f3 = rec[(size_t)r * 4 + 3];
+      const float4 f0 = rec[(size_t)r * 4 + 0];
+      const float4 f1 = rec[(size_t)r * 4 + 1];
+      const float4 f2 = rec[(size_t)r * 4 + 2];
+      const float4 f3 = rec[(size_t)r * 4 + 3];
       s_rec[tid][0] = f0;
       s_rec[tid][1] = f1;
       s_rec[tid][2] = f2;
       s_rec[tid][3] = f3;
-      s_mask[tid] = warp_mask(f0, f3, tx0f, ty0f);
+      s_mask[tid] = warp_mask(f0, f1, f3, tx0f, ty0f);
       s_ridx[tid] = r;
     }
     __syncthreads();
@@ -229,82 +299,59 @@ __global__ void __launch_bounds__(kThreads) k_raster_bwd(ViewTable vt, RenderOpt
         const float vv = fmaf(f1.z, dx, f1.y * dy);
         const float r2 = fmaf(u, u, vv * vv);
         const bool act = pos < nl && r2 < 1.0f;
-        if (!__any_sync(0xffffffffu, act)) continue;
-        float G[16];
+        const uint32_t amask = __ballot_sync(0xffffffffu, act);
+        if (amask == 0u) continue;
+        float G[kGrad2d];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) G[q] = 0.0f;
+        for (int q = 0; q < kGrad2d; ++q) G[q] = 0.0f;
         if (act) {
           const float4 f2 = s_rec[s][2];
           const float4 f3 = s_rec[s][3];
-          const float beta = f1.w, o = f3.z;
+          const float beta = f1.w, inv_o = f3.z;
           const float base = 1.0f - r2;
           const float lb = lg2_approx(base);
-          const float B = ex2_approx(beta * lb);
-          const float a0 = o * B;
+          const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
           const float a = fminf(a0, amax);
-          const float inv = __frcp_rn(1.0f - a);
+          const float inv = rcp_approx(1.0f - a);
           const float Tk = T * inv;
-          const float gc = gx * f2.y + gy * f2.z + gz * f2.w;
-          const float dLa = Tk * gc - GS * inv;
-          GS = fmaf(a * Tk, gc, GS);
+          const float gc = fmaf(gx, f2.y, fmaf(gy, f2.z, gz * f2.w));
+          const float dLa = fmaf(Tk, gc, -GS * inv);
           const float wgt = a * Tk;
+          GS = fmaf(wgt, gc, GS);
           G[7] = wgt * gx;
           G[8] = wgt * gy;
           G[9] = wgt * gz;
           if (a0 < amax) {
-            G[5] = dLa * B;                                   // d o
-            G[6] = dLa * a0 * lb * 0.6931471805599453f;        // d beta
-            const float dr2 = -dLa * a0 * beta / base;
-            const float w0 = fmaf(f1.x, u, f1.z * vv);         // Sigma'^-1 d
+            const float t = dLa * a0;
+            G[5] = a0 > 0.0f ? t * inv_o : 0.0f;              // d o     (B = alpha / o)
+            G[6] = t * lb * 0.6931471805599453f;              // d beta  (alpha ln(1 - r^2))
+            const float dr2 = -t * beta * rcp_approx(base);   // dL/dr^2
+            const float w0 = fmaf(f1.x, u, f1.z * vv);        // Sigma'^-1 d
             const float w1 = f1.y * vv;
-            G[0] = -2.0f * dr2 * w0;                          // d mu'_x
-            G[1] = -2.0f * dr2 * w1;                          // d mu'_y
+            const float m2 = -2.0f * dr2;
+            G[0] = m2 * w0;                                   // d mu'_x
+            G[1] = m2 * w1;                                   // d mu'_y
             G[2] = -dr2 * w0 * w0;                            // d Sigma'_xx
-            G[3] = -2.0f * dr2 * w0 * w1;                     // d Sigma'_xy
+            G[3] = m2 * w0 * w1;                              // d Sigma'_xy
             G[4] = -dr2 * w1 * w1;                            // d Sigma'_yy
           }
           T = Tk;
         }
-        // reduce-scatter butterfly over 16 slots
+        float* gdst = grad2d + (size_t)s_ridx[s] * kGrad2d;
+        if (__popc(amask) <= 2) {
+          // few lanes: direct atomics beat the cross-lane reduction
+          if (act) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const bool up = lane & 16;
-          const float send = up ? G[q] : G[q + 8];
-          const float keep = up ? G[q + 8] : G[q];
-          G[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            for (int q = 0; q < kGrad2d; ++q)
+              if (G[q] != 0.0f) atomicAdd(gdst + q, G[q]);
+          }
+        } else {
+          const float tot = warp_sum10(G, lane);
+          if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const bool up = lane & 8;
-          const float send = up ? G[q] : G[q + 4];
-          const float keep = up ? G[q + 4] : G[q];
-          G[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-        }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const bool up = lane & 4;
-          const float send = up ? G[q] : G[q + 2];
-          const float keep = up ? G[q + 2] : G[q];
-          G[q] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-        }
-        {
-          const bool up = lane & 2;
-          const float send = up ? G[0] : G[1];
-          const float keep = up ? G[1] : G[0];
-          G[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-        }
-        G[0] += __shfl_xor_sync(0xffffffffu, G[0], 1);
-        const int slot = ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-        if (!(lane & 1) && slot < kGrad2d && G[0] != 0.0f)
-          atomicAdd(grad2d + (size_t)s_ridx[s] * kGrad2d + slot, G[0]);
       }
     }
   }
-}
-
-__global__ void k_zero(float4* __restrict__ p, int64_t n4) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // L1 loss: one thread per pixel; block partial sums then a deterministic
@@ -383,15 +430,6 @@ cudaError_t launch_raster_bwd(const ViewTable& vt, const RenderOpts& ro, const f
   if (vt.total_tiles <= 0) return cudaSuccess;
   k_raster_bwd<<<vt.total_tiles, kThreads, 0, s>>>(vt, ro, rec, vals, ranges, T_final, n_contrib,
                                                    dL_dcolor, grad2d, status);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_zero(float* p, int64_t n, cudaStream_t s) {
-  // n is a multiple of 4 (pitch % 4 == 0) and p is 16-byte aligned
-  if (n <= 0) return cudaSuccess;
-  int64_t n4 = n / 4;
-  int grid = (int)std::min<int64_t>((n4 + 255) / 256, 152 * 8);
-  k_zero<<<grid, 256, 0, s>>>((float4*)p, n4);
   return cudaGetLastError();
 }
 

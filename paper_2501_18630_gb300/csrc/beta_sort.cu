@@ -32,6 +32,7 @@ constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 20;
 constexpr int kMaxPasses = 4;
+constexpr int kOnesweepSmem = 2 * kSortTile * 4;  // staged keys + values (32 KB)
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -122,13 +123,13 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
   __shared__ uint32_t h[kMaxPasses][256];
   int64_t count = d_count ? min(*d_count, cap) : count_host;
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
-  // clear the look-back entries of the tiles this sort will use
-  int64_t nblk = (count + kSortTile - 1) / kSortTile;
-  int64_t nclear = (int64_t)npass * look_stride_tiles * 256;
-  int64_t used = nblk * 256;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nclear;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (i % (look_stride_tiles * 256) < used) look[i] = 0;
+  // clear the look-back entries of the tiles this sort will use (per pass)
+  const int64_t nblk = (count + kSortTile - 1) / kSortTile;
+  const int64_t used = nblk * 256;
+  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+  for (int p = 0; p < npass; ++p) {
+    uint32_t* lp = look + (int64_t)p * look_stride_tiles * 256;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < used; i += gstride) lp[i] = 0;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -150,15 +151,24 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
   }
 }
 
-// One onesweep scatter pass over 8-bit digit `shift/8`.
+// One onesweep scatter pass over the 8-bit digit at `shift`.  Each CTA tile
+// of 4096 keys is ranked per warp (match_any), its digit counts are chained
+// to the preceding tiles by decoupled look-back, the keys are reordered by
+// digit in shared memory, and then written out so that consecutive threads
+// write consecutive addresses of each digit's run.
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int write_keys,
     const uint32_t* __restrict__ ghist, uint32_t* look, uint32_t* tile_counter, int64_t count_host,
     const int64_t* __restrict__ d_count, int64_t cap, int shift, int32_t* status) {
+  extern __shared__ uint32_t s_dyn[];
+  uint32_t* s_key = s_dyn;                    // [kSortTile] keys in block-sorted order
+  uint32_t* s_val = s_dyn + kSortTile;        // [kSortTile]
   __shared__ uint32_t s_whist[kSortThreads / 32][256];
-  __shared__ uint32_t s_gbase[256];
+  __shared__ uint32_t s_gbase[256];           // global start of each digit's run for this tile
+  __shared__ uint32_t s_bexcl[256];           // start of each digit inside the tile
   __shared__ uint32_t s_gexcl[256];
+  __shared__ uint32_t s_wsum[kSortThreads / 32];
   __shared__ uint32_t s_tile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t count = d_count ? min(*d_count, cap) : count_host;
@@ -166,17 +176,17 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 
   // exclusive scan of the global digit histogram (once per CTA)
   {
-    uint32_t c = ghist[tid];
+    const uint32_t c = ghist[tid];
     uint32_t x = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) s_gbase[warp] = x;
+    if (lane == 31) s_wsum[warp] = x;
     __syncthreads();
     uint32_t wpre = 0;
-    for (int w = 0; w < warp; ++w) wpre += s_gbase[w];
+    for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
     s_gexcl[tid] = wpre + x - c;
     __syncthreads();
   }
@@ -194,33 +204,47 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      int64_t idx = seg + it * 32 + lane;
-      bool valid = idx < count;
+      const int64_t idx = seg + it * 32 + lane;
+      const bool valid = idx < count;
       key[it] = valid ? keys_in[idx] : 0xffffffffu;
       val[it] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
     }
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      int64_t idx = seg + it * 32 + lane;
-      bool valid = idx < count;
-      uint32_t d = valid ? ((key[it] >> shift) & 255u) : 256u;
-      uint32_t peers = __match_any_sync(0xffffffffu, d);
-      uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-      int leader = __ffs(peers) - 1;
-      uint32_t base = valid ? s_whist[warp][d & 255u] : 0u;
+      const int64_t idx = seg + it * 32 + lane;
+      const bool valid = idx < count;
+      const uint32_t d = valid ? ((key[it] >> shift) & 255u) : 256u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+      const int leader = __ffs(peers) - 1;
+      const uint32_t base = valid ? s_whist[warp][d & 255u] : 0u;
       __syncwarp();
       if (valid && lane == leader) s_whist[warp][d] = base + (uint32_t)__popc(peers);
       __syncwarp();
       loc[it] = base + rank;
     }
     __syncthreads();
-    // per digit: exclusive prefix over warps, CTA total
+    // per digit (thread tid): exclusive prefix over warps and the tile total
     uint32_t total = 0;
 #pragma unroll
     for (int w = 0; w < kSortThreads / 32; ++w) {
-      uint32_t c = s_whist[w][tid];
+      const uint32_t c = s_whist[w][tid];
       s_whist[w][tid] = total;
       total += c;
+    }
+    // start of digit tid inside the tile: exclusive scan of the totals
+    {
+      uint32_t x = total;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) s_wsum[warp] = x;
+      __syncthreads();
+      uint32_t wpre = 0;
+      for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+      s_bexcl[tid] = wpre + x - total;
     }
     // decoupled look-back for digit `tid`
     uint32_t* my = look + tile * 256 + tid;
@@ -250,15 +274,27 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     }
     s_gbase[tid] = s_gexcl[tid] + excl;
     __syncthreads();
+    // reorder by digit inside the tile
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      int64_t idx = seg + it * 32 + lane;
+      const int64_t idx = seg + it * 32 + lane;
       if (idx < count) {
-        uint32_t d = (key[it] >> shift) & 255u;
-        uint32_t pos = s_gbase[d] + s_whist[warp][d] + loc[it];
-        if (write_keys) keys_out[pos] = key[it];
-        vals_out[pos] = val[it];
+        const uint32_t d = (key[it] >> shift) & 255u;
+        const uint32_t pos = s_bexcl[d] + s_whist[warp][d] + loc[it];
+        s_key[pos] = key[it];
+        s_val[pos] = val[it];
       }
+    }
+    __syncthreads();
+    // coalesced write-out: element i of the tile goes to its digit's run
+    const int n_here = (int)min((int64_t)kSortTile, count - tile * kSortTile);
+#pragma unroll 4
+    for (int i = tid; i < n_here; i += kSortThreads) {
+      const uint32_t k = s_key[i];
+      const uint32_t d = (k >> shift) & 255u;
+      const uint32_t gpos = s_gbase[d] + ((uint32_t)i - s_bexcl[d]);
+      if (write_keys) keys_out[gpos] = k;
+      vals_out[gpos] = s_val[i];
     }
     __syncthreads();
   }
@@ -448,7 +484,7 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
   int grid_d = (int)std::min<int64_t>(nblk_d, persist);
   if (grid_d < 1) grid_d = 1;
   for (int p = 0; p < 4; ++p) {
-    k_onesweep<<<grid_d, kSortThreads, 0, s>>>(kin, vin, kbuf[p & 1], vbuf[p & 1], p < 3 ? 1 : 0,
+    k_onesweep<<<grid_d, kSortThreads, kOnesweepSmem, s>>>(kin, vin, kbuf[p & 1], vbuf[p & 1], p < 3 ? 1 : 0,
                                                gh_d + p * 256, w.look_d + (size_t)p * nblk_d * 256,
                                                w.counters + p, n_items, nullptr, n_items, 8 * p,
                                                d_status);
@@ -483,7 +519,7 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
     const uint32_t* ki = w.pkey_a;
     const uint32_t* vi = pval_emit;
     for (int p = 0; p < np_t; ++p) {
-      k_onesweep<<<grid_t, kSortThreads, 0, s>>>(ki, vi, pk[p & 1], pv[p & 1], 1,
+      k_onesweep<<<grid_t, kSortThreads, kOnesweepSmem, s>>>(ki, vi, pk[p & 1], pv[p & 1], 1,
                                                  gh_t + p * 256, w.look_t + (size_t)p * nblk_t * 256,
                                                  w.counters + kMaxPasses + p, 0, d_count, cap, 8 * p,
                                                  d_status);
