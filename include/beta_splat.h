@@ -3,7 +3,7 @@
  *
  * Deformable Beta Splatting (arXiv 2501.18630): 3D ellipsoidal Beta
  * primitives {mu, o, q, s, b, f} (Sec. 3.2) are projected with EWA
- * (Sigma' = J W Sigma W^T J^T), binned into 16x16 pixel tiles, depth-sorted,
+ * (Sigma' = J W Sigma W^T J^T), binned into pixel tiles (16x16 by default), depth-sorted,
  * and composited front to back with the Beta kernel
  *     alpha = min(alpha_max, o (1 - r^2)^beta),  beta = 4 e^b    (Eq. 2, Eq. eq:beta)
  *     C(x) = sum_i c_i alpha_i prod_{j<i} (1 - alpha_j)              (Eq. C)
@@ -92,7 +92,7 @@ typedef struct {
 
 /* Render options (host struct).  beta_default_opts() fills the defaults. */
 typedef struct {
-  int32_t tile_w, tile_h; /* pixel tile; 16 x 16 is the supported shape      */
+  int32_t tile_w, tile_h; /* pixel tile: 8x8, 16x8, 16x16 (default) or 32x16   */
   int32_t batch_s;        /* records staged per raster batch: 64, 128 or 256 */
   int32_t color_mode;     /* 0: c0 + lobes, 1: c0 only (diffuse), 2: lobes only (specular) */
   float t_eps;            /* stop before a primitive once T < t_eps (2^-19)   */
@@ -181,15 +181,27 @@ int beta_bin_sort_static(const beta_params* prm, const beta_camera* cams, int32_
                          int64_t pair_capacity, uint32_t* tile_ranges, int64_t* d_pair_count,
                          int32_t* d_status, beta_stream_t stream);
 
+/* Longest-first tile schedule for the persistent raster kernels.  Reads the
+ * tile ranges written by beta_bin_sort and writes into `sched`
+ * (beta_schedule_bytes() bytes, 4-byte aligned): the tiles ordered by
+ * decreasing pair count (bucketed by bit length) and two work counters that
+ * the raster kernels consume and reset.  Without a schedule (sched = NULL in
+ * the raster calls) CTA b renders tile b. */
+size_t beta_schedule_bytes(const beta_camera* cams /* host */, int32_t n_views, const beta_opts* opt);
+int beta_schedule(const beta_camera* cams, int32_t n_views, const beta_opts* opt,
+                  const uint32_t* tile_ranges, void* sched, const int32_t* d_status,
+                  beta_stream_t stream);
+
 /* Step 3 (Eq. C): front-to-back compositing of every tile's sorted list.
  *   color     [3 x total_pixels] out: C + T_final * bg (planar per view)
  *   T_final   [total_pixels] out: final transmittance
  *   n_contrib [total_pixels] out: 1 + position (inside the tile's list) of
  *             the last primitive that contributed, 0 if none.
+ *   sched     beta_schedule() output for a persistent launch, or NULL
  *   d_status  in: if non-zero the kernel writes nothing. */
 int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                    const uint32_t* tile_ranges, float* color, float* T_final,
+                    const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
                     uint32_t* n_contrib, const int32_t* d_status, beta_stream_t stream);
 
 /* Per-pixel L1 loss of a batch of views (Sec. 3.4, the L1 term):
@@ -204,13 +216,14 @@ int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color,
  * contributor down, recovering T by division, and accumulates per-record 2D
  * gradients (d mu' (2), d Sigma' (a, b, c), d o, d beta, d colour (3)) with
  * warp-reduced atomics into grad2d.
+ *   sched     beta_schedule() output (persistent launch) or NULL
  *   dL_dcolor [3 x total_pixels] in (layout of color)
  *   grad2d    [beta_grad2d_bytes()] in/out: 10 floats per record, ACCUMULATED.
  *             It must hold zeros on entry: zero it once after allocation;
  *             beta_project_bwd clears every slot it consumes. */
 int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                    const uint32_t* tile_ranges, const float* T_final,
+                    const uint32_t* tile_ranges, void* sched, const float* T_final,
                     const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
                     const int32_t* d_status, beta_stream_t stream);
 

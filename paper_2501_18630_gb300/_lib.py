@@ -29,7 +29,8 @@ EXPORTS = [
     "beta_default_opts", "beta_status_string", "beta_version", "beta_proj_bytes",
     "beta_total_tiles", "beta_total_pixels", "beta_binsort_workspace_bytes", "beta_grad2d_bytes",
     "beta_l1_workspace_bytes", "beta_project", "beta_bin_sort", "beta_raster_fwd", "beta_l1_loss",
-    "beta_raster_bwd", "beta_project_bwd", "beta_bin_sort_static",
+    "beta_raster_bwd", "beta_project_bwd", "beta_bin_sort_static", "beta_schedule_bytes",
+    "beta_schedule",
 ]
 
 
@@ -85,9 +86,11 @@ def load(path: str = LIB_PATH):
             "beta_l1_workspace_bytes": (sz, [C, i32]),
             "beta_project": (ctypes.c_int, [P, C, i32, O, vp, vp]),
             "beta_bin_sort": (ctypes.c_int, [P, C, i32, O, vp, vp, i64, vp, vp, vp, vp, sz, vp]),
-            "beta_raster_fwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "beta_raster_fwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
             "beta_l1_loss": (ctypes.c_int, [C, i32, vp, vp, vp, vp, vp, sz, vp]),
-            "beta_raster_bwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "beta_raster_bwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "beta_schedule_bytes": (sz, [C, i32, O]),
+            "beta_schedule": (ctypes.c_int, [C, i32, O, vp, vp, vp, vp]),
             "beta_project_bwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp]),
             "beta_bin_sort_static": (ctypes.c_int, [P, C, i32, O, vp, vp, i64, vp, vp, vp, vp]),
         }

@@ -1,0 +1,92 @@
+"""Autotuner for the batched raster step: picks the tile shape, the number of
+records staged per batch and persistent vs one-CTA-per-tile scheduling by
+timing each candidate's captured CUDA graph on the actual workload.
+
+Results are cached in a JSON file keyed by (primitive count, lobes, view
+resolutions, device name), so a workload is tuned once per machine.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import torch
+
+from . import _lib
+from .batched import BatchedStep
+
+# (tile_w, tile_h, batch_s, persistent)
+CANDIDATES = [
+    (16, 16, 256, True), (16, 16, 128, True), (16, 16, 64, True), (16, 16, 256, False),
+    (16, 8, 128, True), (16, 8, 64, True), (32, 16, 256, True), (8, 8, 64, True),
+]
+
+
+def cache_path() -> str:
+    base = os.environ.get("BETA_AUTOTUNE_CACHE")
+    if base:
+        return base
+    return os.path.join(os.path.expanduser("~"), ".cache", "paper_2501_18630_gb300", "autotune.json")
+
+
+def workload_key(n: int, n_lobes: int, cameras, device) -> str:
+    res = ",".join(f"{c.width}x{c.height}" for c in cameras)
+    return f"n={n};M={n_lobes};views={res};dev={torch.cuda.get_device_name(device)}"
+
+
+def _load():
+    try:
+        with open(cache_path()) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def _save(d):
+    p = cache_path()
+    os.makedirs(os.path.dirname(p), exist_ok=True)
+    tmp = p + f".tmp{os.getpid()}"
+    with open(tmp, "w") as fh:
+        json.dump(d, fh, indent=1, sort_keys=True)
+    os.replace(tmp, p)
+
+
+def time_candidate(planes, n, n_lobes, cameras, target, cand, reps=5):
+    tw, th, s, persist = cand
+    opts = _lib.default_opts(tile_w=tw, tile_h=th, batch_s=s)
+    step = BatchedStep(planes, n, n_lobes, cameras, target, opts=opts, persistent=persist)
+    step.step()
+    step.check()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        step.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del step
+    torch.cuda.empty_cache()
+    return ms
+
+
+def tune(planes, n, n_lobes, cameras, target, candidates=None, reps=5, use_cache=True, log=None):
+    """Returns (best candidate, {candidate: ms}).  Candidates are tuples
+    (tile_w, tile_h, batch_s, persistent)."""
+    key = workload_key(n, n_lobes, cameras, planes.device)
+    cache = _load() if use_cache else {}
+    if use_cache and key in cache:
+        e = cache[key]
+        return tuple(e["best"]), {tuple(json.loads(k)): v for k, v in e["times"].items()}
+    times = {}
+    for cand in (candidates or CANDIDATES):
+        t0 = time.perf_counter()
+        times[tuple(cand)] = time_candidate(planes, n, n_lobes, cameras, target, cand, reps)
+        if log:
+            log(f"autotune {cand}: {times[tuple(cand)]:.3f} ms ({time.perf_counter() - t0:.1f} s)")
+    best = min(times, key=times.get)
+    if use_cache:
+        cache[key] = {"best": list(best), "times": {json.dumps(list(k)): v for k, v in times.items()}}
+        _save(cache)
+    return best, times

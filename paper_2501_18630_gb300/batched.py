@@ -1,0 +1,82 @@
+"""Batched forward + backward of many views as one replayable CUDA graph.
+
+The whole step -- project, bin/sort, longest-first schedule, persistent
+raster forward, per-view L1 loss, persistent raster backward, projection
+backward -- is captured once and replayed.  Every entry point only enqueues
+kernels and the pair count stays on the device, so nothing in the step
+synchronises with the host.  A pair-capacity overflow shows up in the device
+status word; check() reads it (one sync), grows the buffers and recaptures.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import _lib
+from .render import Rasterizer
+
+
+class BatchedStep:
+    def __init__(self, planes: torch.Tensor, n: int, n_lobes: int, cameras, target: torch.Tensor,
+                 opts: _lib.BetaOpts | None = None, persistent: bool = True, headroom: float = 1.15):
+        self.planes = planes
+        self.target = target
+        self.rast = Rasterizer(n, planes.shape[1], n_lobes, cameras, opts, device=planes.device,
+                               persistent=persistent)
+        self.grad = torch.zeros_like(planes)
+        self.headroom = headroom
+        self.graph = None
+        self._size_pairs()
+
+    def _size_pairs(self):
+        r = self.rast
+        r.forward(self.planes, check_capacity=True)
+        _, k = r.device_status()
+        r._alloc_pairs(int(math.ceil(k * self.headroom)) + 65536)
+
+    def body(self):
+        """The step as eager launches on the current stream."""
+        r = self.rast
+        r.project(self.planes)
+        r.bin_sort(self.planes)
+        if r.persistent:
+            r.schedule()
+        r.raster_fwd(self.planes)
+        r.l1_loss(self.target)
+        r.raster_bwd(self.planes, r.dL_dcolor)
+        r.project_bwd(self.planes, self.grad)
+
+    def capture(self):
+        side = torch.cuda.Stream(device=self.planes.device)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self.body()                       # warm-up outside the graph (lazy module loading)
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.body()
+        self.graph = g
+        return g
+
+    def step(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+
+    def check(self) -> int:
+        """Reads the device status after a replay; on a capacity overflow grows
+        the pair buffers, recaptures and replays.  Returns the pair count."""
+        st, k = self.rast.device_status()
+        if st == _lib.BETA_ERR_CAPACITY:
+            self.rast._alloc_pairs(int(math.ceil(k * self.headroom)) + 65536)
+            self.graph = None
+            self.step()
+            st, k = self.rast.device_status()
+        if st != _lib.BETA_OK:
+            raise _lib.BetaError("batched step", st, _lib.load().beta_status_string(st).decode())
+        return k
+
+    @property
+    def loss(self):
+        return self.rast.loss

@@ -28,7 +28,8 @@ bool valid_params(const beta_params* p) {
 
 int check_opts(const beta_opts* o) {
   if (!o) return BETA_ERR_ARG;
-  if (o->tile_w != 16 || o->tile_h != 16) return BETA_ERR_UNSUPPORTED;
+  const int shape = o->tile_w * 1000 + o->tile_h;
+  if (shape != 8008 && shape != 16008 && shape != 16016 && shape != 32016) return BETA_ERR_UNSUPPORTED;
   if (o->batch_s != 64 && o->batch_s != 128 && o->batch_s != 256) return BETA_ERR_UNSUPPORTED;
   if (o->color_mode < 0 || o->color_mode > 2) return BETA_ERR_ARG;
   if (!(o->t_eps >= 0.0f && o->t_eps < 1.0f)) return BETA_ERR_ARG;
@@ -88,6 +89,9 @@ RenderOpts render_opts(const beta_opts* o) {
   r.b_lo = o->b_lo;
   r.b_hi = o->b_hi;
   r.color_mode = o->color_mode;
+  r.tile_w = o->tile_w;
+  r.tile_h = o->tile_h;
+  r.batch_s = o->batch_s;
   return r;
 }
 
@@ -245,7 +249,7 @@ int beta_bin_sort_static(const beta_params* prm, const beta_camera* cams, int32_
 
 int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                    const uint32_t* tile_ranges, float* color, float* T_final,
+                    const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
                     uint32_t* n_contrib, const int32_t* d_status, beta_stream_t stream) {
   if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !color || !T_final ||
       !n_contrib || !d_status)
@@ -255,8 +259,27 @@ int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
   ViewTable vt;
   if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
   ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
+  if (sched && ((uintptr_t)sched & 3u)) return BETA_ERR_ARG;
   return cuda_status(launch_raster_fwd(vt, render_opts(opt), pb.rec, pair_vals, tile_ranges, color,
-                                       T_final, n_contrib, d_status, (cudaStream_t)stream));
+                                       T_final, n_contrib, d_status, (uint32_t*)sched,
+                                       (cudaStream_t)stream));
+}
+
+size_t beta_schedule_bytes(const beta_camera* cams, int32_t n_views, const beta_opts* opt) {
+  ViewTable vt;
+  if (check_opts(opt) != BETA_OK || build_views(cams, n_views, opt, vt) != BETA_OK) return 0;
+  return schedule_bytes(vt.total_tiles);
+}
+
+int beta_schedule(const beta_camera* cams, int32_t n_views, const beta_opts* opt,
+                  const uint32_t* tile_ranges, void* sched, const int32_t* d_status,
+                  beta_stream_t stream) {
+  if (!tile_ranges || !sched || !d_status || ((uintptr_t)sched & 3u)) return BETA_ERR_ARG;
+  int e = check_opts(opt);
+  if (e != BETA_OK) return e;
+  ViewTable vt;
+  if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  return cuda_status(launch_schedule(vt, tile_ranges, (uint32_t*)sched, d_status, (cudaStream_t)stream));
 }
 
 int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color, const float* target,
@@ -273,7 +296,7 @@ int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color, c
 
 int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                    const uint32_t* tile_ranges, const float* T_final,
+                    const uint32_t* tile_ranges, void* sched, const float* T_final,
                     const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
                     const int32_t* d_status, beta_stream_t stream) {
   if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !T_final || !n_contrib ||
@@ -284,9 +307,10 @@ int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
   ViewTable vt;
   if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
   ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
+  if (sched && ((uintptr_t)sched & 3u)) return BETA_ERR_ARG;
   return cuda_status(launch_raster_bwd(vt, render_opts(opt), pb.rec, pair_vals, tile_ranges,
                                        T_final, n_contrib, dL_dcolor, grad2d, d_status,
-                                       (cudaStream_t)stream));
+                                       (uint32_t*)sched, (cudaStream_t)stream));
 }
 
 int beta_project_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,

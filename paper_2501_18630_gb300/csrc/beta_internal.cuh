@@ -42,6 +42,7 @@ struct ViewTable {
 struct RenderOpts {
   float t_eps, alpha_max, blur_eps, b_lo, b_hi;
   int32_t color_mode;
+  int32_t tile_w, tile_h, batch_s;
 };
 
 // status helpers -------------------------------------------------------------
@@ -167,7 +168,7 @@ __device__ __forceinline__ bool rule_depth(const PrimGeo& pg, const ViewDev& V, 
 // Rule chain, per-view part after rule_depth: J, M, diagonal of Sigma' and
 // the tile rectangle.  Returns false if the rectangle is empty.
 __device__ __forceinline__ bool rule_view(const PrimGeo& pg, const ViewDev& V, float blur,
-                                          ViewGeo& g, int rect[4]) {
+                                          int tile_w, int tile_h, ViewGeo& g, int rect[4]) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -211,10 +212,10 @@ __device__ __forceinline__ bool rule_view(const PrimGeo& pg, const ViewDev& V, f
   if (i1 > wm1) i1 = wm1;
   if (j1 > hm1) j1 = hm1;
   if (i0 > i1 || j0 > j1) return false;
-  rect[0] = (int)i0 / 16;
-  rect[1] = (int)i1 / 16;
-  rect[2] = (int)j0 / 16;
-  rect[3] = (int)j1 / 16;
+  rect[0] = (int)i0 / tile_w;
+  rect[1] = (int)i1 / tile_w;
+  rect[2] = (int)j0 / tile_h;
+  rect[3] = (int)j1 / tile_h;
   return true;
 }
 
@@ -316,11 +317,14 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
 cudaError_t launch_raster_fwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                               const uint32_t* vals, const uint32_t* ranges, float* color,
                               float* T_final, uint32_t* n_contrib, const int32_t* status,
-                              cudaStream_t s);
+                              uint32_t* sched, cudaStream_t s);
 cudaError_t launch_raster_bwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                               const uint32_t* vals, const uint32_t* ranges, const float* T_final,
                               const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
-                              const int32_t* status, cudaStream_t s);
+                              const int32_t* status, uint32_t* sched, cudaStream_t s);
+size_t schedule_bytes(int total_tiles);
+cudaError_t launch_schedule(const ViewTable& vt, const uint32_t* ranges, uint32_t* sched,
+                            const int32_t* status, cudaStream_t s);
 size_t l1_ws_bytes(const ViewTable& vt);
 cudaError_t launch_l1(const ViewTable& vt, const float* color, const float* target, float* loss,
                       float* dL_dcolor, float* ws, cudaStream_t s);

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
     ViewGeo g;
     int rc[4];
     uint32_t kk = 0xffffffffu;
-    bool bin = ok && rule_depth(pg, V, g, kk) && rule_view(pg, V, ro.blur_eps, g, rc);
+    bool bin = ok && rule_depth(pg, V, g, kk) && rule_view(pg, V, ro.blur_eps, ro.tile_w, ro.tile_h, g, rc);
     float4 o0, o1, o2, o3;
     if (bin) {
       // projected centre in double-float
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
       ViewGeo g;
       int rc[4];
       uint32_t kk;
-      if (!rule_depth(pg, V, g, kk) || !rule_view(pg, V, ro.blur_eps, g, rc)) continue;
+      if (!rule_depth(pg, V, g, kk) || !rule_view(pg, V, ro.blur_eps, ro.tile_w, ro.tile_h, g, rc)) continue;
       const float gmx = G[0], gmy = G[1], ga = G[2], gb = G[3], gc = G[4];
       // Sigma' = M M^T: dM0 = 2 ga M0 + gb M1, dM1 = gb M0 + 2 gc M1
       float dM0[3], dM1[3];

@@ -1,26 +1,30 @@
 // beta_raster.cu -- tile compositing (forward), its reverse-order backward,
-// and the per-pixel L1 loss.
+// the per-pixel L1 loss, and the longest-first tile schedule.
 //
-// Forward (Eq. C of arXiv 2501.18630): for every pixel of a 16x16 tile, walk
-// the tile's depth-sorted list, r^2 = (p dx)^2 + (q2 dx + q1 dy)^2, and for
+// Forward (Eq. C of arXiv 2501.18630): for every pixel of a tile, walk the
+// tile's depth-sorted list, r^2 = (p dx)^2 + (q2 dx + q1 dy)^2, and for
 // r^2 < 1 (the Beta kernel's bounded support, Eq. 2) composite
 //   alpha = min(alpha_max, o (1 - r^2)^beta),  C += T alpha c,  T *= 1 - alpha,
 // stopping before a primitive once T < t_eps.
 //
-// Layout: one CTA of 256 threads per tile, one pixel per thread; warp w owns
-// the 8x4 pixel block (8 (w & 1), 4 (w >> 1)).  Records are staged 256 at a
-// time in shared memory together with an 8-bit mask of the warp blocks their
-// support box overlaps; each warp walks only the records of its mask bit
-// (ballot over 32 records), so whole warps skip records that cannot touch
+// Layout: one CTA per TW x TH tile, one pixel per thread; warp w owns an 8x4
+// pixel block.  Records are staged S at a time in shared memory together with
+// a mask of the warp blocks their support ellipse can reach (an exact
+// ellipse-vs-rectangle test); each warp walks only the records of its mask
+// bit (ballot over 32 records), so whole warps skip records that cannot touch
 // them.  Transmittance early exit is decided per warp (__all_sync) and per
 // CTA (__syncthreads_or).
 //
 // Backward: the same tiling walks each tile list from the largest
 // last-contributor position down, recovering T_k = T_{k+1} / (1 - alpha_k)
 // and the suffix colour S (as g . S), and produces per-record 2D gradients
-// (d mu', d Sigma', d o, d beta, d colour).  A warp sums its 32 lanes'
-// 10 values with a 16-slot reduce-scatter butterfly (16 shuffles instead of
-// 50) and one atomic per value goes to the record's slot in grad2d.
+// (d mu', d Sigma', d o, d beta, d colour); a warp sums its lanes' ten values
+// with a 12-shuffle reduce-scatter and issues one atomic per value.
+//
+// Scheduling: with a schedule buffer (beta_schedule) the raster kernels are
+// persistent -- a grid sized to the SMs takes tiles from a global counter in
+// longest-list-first order (tiles bucketed by floor(log2 count)); the last
+// CTA to leave resets the counter.  Without one, CTA b renders tile b.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -50,18 +54,20 @@ __device__ __forceinline__ float r2_at(float p, float q1, float q2, float dx, fl
 // minimum of the convex r^2 over the block's rectangle of pixel centres is at
 // the ellipse centre if it lies inside, else on an edge, where it is the
 // clamped 1D minimiser.
-__device__ __forceinline__ uint8_t warp_mask(float4 f0, float4 f1, float4 f3, float tx0f, float ty0f) {
+template <int TW, int TH>
+__device__ __forceinline__ uint32_t warp_mask(float4 f0, float4 f1, float4 f3, float tx0f, float ty0f) {
+  constexpr int NW = TW * TH / 32, BXW = TW / 8;
   // centre relative to the tile origin, in pixel-index coordinates
   const float rx = (f0.x - tx0f) - f0.z;
   const float ry = (f0.y - ty0f) - f0.w;
   const float ex = f3.x, ey = f3.y;
   const float p = f1.x, q1 = f1.y, q2 = f1.z;
-  const float kv = -q2 / q1;                        // dy minimising r^2 at fixed dx, per unit dx
+  const float kv = -q2 / q1;                          // dy minimising r^2 at fixed dx, per unit dx
   const float kh = -(q1 * q2) / fmaf(p, p, q2 * q2);  // dx minimising r^2 at fixed dy, per unit dy
   uint32_t m = 0;
 #pragma unroll
-  for (int w = 0; w < 8; ++w) {
-    const float bx = 8.0f * (w & 1), by = 4.0f * (w >> 1);
+  for (int w = 0; w < NW; ++w) {
+    const float bx = 8.0f * (w % BXW), by = 4.0f * (w / BXW);
     const float x0 = bx - rx, x1 = bx + 7.0f - rx, y0 = by - ry, y1 = by + 3.0f - ry;
     if (x1 < -ex || x0 > ex || y1 < -ey || y0 > ey) continue;   // bounding box misses the block
     bool hit = (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f);
@@ -74,97 +80,132 @@ __device__ __forceinline__ uint8_t warp_mask(float4 f0, float4 f1, float4 f3, fl
     }
     if (hit) m |= 1u << w;
   }
-  return (uint8_t)m;
+  return m;
 }
 
-__global__ void __launch_bounds__(kThreads) k_raster_fwd(ViewTable vt, RenderOpts ro,
-                                                         const float4* __restrict__ rec,
-                                                         const uint32_t* __restrict__ vals,
-                                                         const uint32_t* __restrict__ ranges,
-                                                         float* __restrict__ color,
-                                                         float* __restrict__ Tout,
-                                                         uint32_t* __restrict__ ncontrib,
-                                                         const int32_t* __restrict__ status) {
-  __shared__ float4 s_rec[kThreads][3];
-  __shared__ uint8_t s_mask[kThreads];
-  if (*status != 0) return;
-  const int g = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int v = view_of_tile(vt, g);
-  const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
-  const int lt = g - vt.v[v].tile_off;
-  const int ty = lt / ntx, tx = lt - ty * ntx;
-  const int x = tx * 16 + (warp & 1) * 8 + (lane & 7);
-  const int y = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
-  const bool inside = x < W && y < H;
-  const float xf = (float)x, yf = (float)y;
-  const float tx0f = (float)(tx * 16), ty0f = (float)(ty * 16);
-  const uint32_t start = ranges[g], end = ranges[g + 1];
-  const float t_eps = ro.t_eps, amax = ro.alpha_max;
+// Tile assignment: CTA b renders tile b, or (persistent) tiles are taken from
+// the schedule's counter in its longest-first order.  Returns -1 when done.
+template <bool PERSIST>
+__device__ __forceinline__ int next_tile(int iter, int total_tiles, uint32_t* ctr,
+                                         const uint32_t* order, int* s_item) {
+  if (!PERSIST) return iter == 0 ? (int)blockIdx.x : -1;
+  if (threadIdx.x == 0) *s_item = (int)atomicAdd(ctr, 1u);
+  __syncthreads();
+  const int item = *s_item;
+  __syncthreads();
+  return item < total_tiles ? (int)order[item] : -1;
+}
 
-  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-  uint32_t last = 0;
-  bool done = !inside;
-  bool warp_done = __all_sync(0xffffffffu, done);
-
-  for (uint32_t base = start; base < end; base += kThreads) {
-    if (!__syncthreads_or(!done)) break;
-    const uint32_t j = base + tid;
-    if (j < end) {
-      const uint32_t r = vals[j];
-      const float4 f0 = rec[(size_t)r * 4 + 0];
-      const float4 f1 = rec[(size_t)r * 4 + 1];
-      const float4 f2 = rec[(size_t)r * 4 + 2];
-      const float4 f3 = rec[(size_t)r * 4 + 3];
-      s_rec[tid][0] = f0;
-      s_rec[tid][1] = f1;
-      s_rec[tid][2] = f2;
-      s_mask[tid] = warp_mask(f0, f1, f3, tx0f, ty0f);
+// The last CTA of a persistent grid to run out of work resets the counter.
+template <bool PERSIST>
+__device__ __forceinline__ void leave(uint32_t* ctr) {
+  if (PERSIST && threadIdx.x == 0) {
+    const uint32_t done = atomicAdd(ctr + 1, 1u);
+    if (done == gridDim.x - 1) {
+      ctr[0] = 0u;
+      ctr[1] = 0u;
     }
-    __syncthreads();
-    const int cnt = (int)min((uint32_t)kThreads, end - base);
-    for (int c = 0; c < cnt && !warp_done; c += 32) {
-      const int idx = c + lane;
-      const bool bit = idx < cnt && ((s_mask[idx] >> warp) & 1u);
-      uint32_t bits = __ballot_sync(0xffffffffu, bit);
-      while (bits) {
-        const int k = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const int s = c + k;
-        const float4 f0 = s_rec[s][0];
-        const float4 f1 = s_rec[s][1];
-        const float dx = (xf - f0.x) + f0.z;
-        const float dy = (yf - f0.y) + f0.w;
-        const float u = f1.x * dx;
-        const float vv = fmaf(f1.z, dx, f1.y * dy);
-        const float r2 = fmaf(u, u, vv * vv);
-        if (!done && r2 < 1.0f) {
-          const float4 f2 = s_rec[s][2];
-          const float lb = lg2_approx(1.0f - r2);
-          float a = ex2_approx(fmaf(f1.w, lb, f2.x));
-          a = fminf(a, amax);
-          const float w = a * T;
-          C0 = fmaf(w, f2.y, C0);
-          C1 = fmaf(w, f2.z, C1);
-          C2 = fmaf(w, f2.w, C2);
-          T = T * (1.0f - a);
-          last = base - start + (uint32_t)s + 1u;
-          done = T < t_eps;
+  }
+}
+
+template <int TW, int TH, int S, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH) k_raster_fwd(ViewTable vt, RenderOpts ro,
+                                                       const float4* __restrict__ rec,
+                                                       const uint32_t* __restrict__ vals,
+                                                       const uint32_t* __restrict__ ranges,
+                                                       float* __restrict__ color,
+                                                       float* __restrict__ Tout,
+                                                       uint32_t* __restrict__ ncontrib,
+                                                       const int32_t* __restrict__ status,
+                                                       uint32_t* ctr, const uint32_t* __restrict__ order) {
+  constexpr int NT = TW * TH, BXW = TW / 8;
+  __shared__ float4 s_rec[S][3];
+  __shared__ uint32_t s_mask[S];
+  __shared__ int s_item;
+  if (*status != 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float t_eps = ro.t_eps, amax = ro.alpha_max;
+  for (int iter = 0;; ++iter) {
+    const int g = next_tile<PERSIST>(iter, vt.total_tiles, ctr, order, &s_item);
+    if (g < 0) break;
+    const int v = view_of_tile(vt, g);
+    const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
+    const int lt = g - vt.v[v].tile_off;
+    const int ty = lt / ntx, tx = lt - ty * ntx;
+    const int x = tx * TW + (warp % BXW) * 8 + (lane & 7);
+    const int y = ty * TH + (warp / BXW) * 4 + (lane >> 3);
+    const bool inside = x < W && y < H;
+    const float xf = (float)x, yf = (float)y;
+    const float tx0f = (float)(tx * TW), ty0f = (float)(ty * TH);
+    const uint32_t start = ranges[g], end = ranges[g + 1];
+
+    float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+    uint32_t last = 0;
+    bool done = !inside;
+    bool warp_done = __all_sync(0xffffffffu, done);
+
+    for (uint32_t base = start; base < end; base += S) {
+      if (!__syncthreads_or(!done)) break;
+      for (int jj = tid; jj < S; jj += NT) {
+        const uint32_t j = base + jj;
+        if (j < end) {
+          const uint32_t r = vals[j];
+          const float4 f0 = rec[(size_t)r * 4 + 0];
+          const float4 f1 = rec[(size_t)r * 4 + 1];
+          const float4 f2 = rec[(size_t)r * 4 + 2];
+          const float4 f3 = rec[(size_t)r * 4 + 3];
+          s_rec[jj][0] = f0;
+          s_rec[jj][1] = f1;
+          s_rec[jj][2] = f2;
+          s_mask[jj] = warp_mask<TW, TH>(f0, f1, f3, tx0f, ty0f);
         }
       }
-      warp_done = __all_sync(0xffffffffu, done);
+      __syncthreads();
+      const int cnt = (int)min((uint32_t)S, end - base);
+      for (int c = 0; c < cnt && !warp_done; c += 32) {
+        const int idx = c + lane;
+        const bool bit = idx < cnt && ((s_mask[idx] >> warp) & 1u);
+        uint32_t bits = __ballot_sync(0xffffffffu, bit);
+        while (bits) {
+          const int k = __ffs(bits) - 1;
+          bits &= bits - 1;
+          const int s = c + k;
+          const float4 f0 = s_rec[s][0];
+          const float4 f1 = s_rec[s][1];
+          const float dx = (xf - f0.x) + f0.z;
+          const float dy = (yf - f0.y) + f0.w;
+          const float u = f1.x * dx;
+          const float vv = fmaf(f1.z, dx, f1.y * dy);
+          const float r2 = fmaf(u, u, vv * vv);
+          if (!done && r2 < 1.0f) {
+            const float4 f2 = s_rec[s][2];
+            const float lb = lg2_approx(1.0f - r2);
+            float a = ex2_approx(fmaf(f1.w, lb, f2.x));
+            a = fminf(a, amax);
+            const float w = a * T;
+            C0 = fmaf(w, f2.y, C0);
+            C1 = fmaf(w, f2.z, C1);
+            C2 = fmaf(w, f2.w, C2);
+            T = T * (1.0f - a);
+            last = base - start + (uint32_t)s + 1u;
+            done = T < t_eps;
+          }
+        }
+        warp_done = __all_sync(0xffffffffu, done);
+      }
+    }
+    if (inside) {
+      const int64_t HW = (int64_t)W * H;
+      const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
+      float* cb = color + 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+      cb[0] = C0 + T * vt.v[v].bg[0];
+      cb[HW] = C1 + T * vt.v[v].bg[1];
+      cb[2 * HW] = C2 + T * vt.v[v].bg[2];
+      Tout[pix] = T;
+      ncontrib[pix] = last;
     }
   }
-  if (inside) {
-    const int64_t HW = (int64_t)W * H;
-    const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
-    float* cb = color + 3 * vt.v[v].pix_off + (int64_t)y * W + x;
-    cb[0] = C0 + T * vt.v[v].bg[0];
-    cb[HW] = C1 + T * vt.v[v].bg[1];
-    cb[2 * HW] = C2 + T * vt.v[v].bg[2];
-    Tout[pix] = T;
-    ncontrib[pix] = last;
-  }
+  leave<PERSIST>(ctr);
 }
 
 // Sum of ten per-lane values over the warp, scattered: on return lane L holds
@@ -214,143 +255,201 @@ __device__ __forceinline__ int warp_sum10_field(int lane) {
   return (b4 ? 5 : 0) + sub;
 }
 
-__global__ void __launch_bounds__(kThreads) k_raster_bwd(ViewTable vt, RenderOpts ro,
-                                                         const float4* __restrict__ rec,
-                                                         const uint32_t* __restrict__ vals,
-                                                         const uint32_t* __restrict__ ranges,
-                                                         const float* __restrict__ Tfin,
-                                                         const uint32_t* __restrict__ ncontrib,
-                                                         const float* __restrict__ dLdC,
-                                                         float* __restrict__ grad2d,
-                                                         const int32_t* __restrict__ status) {
-  __shared__ float4 s_rec[kThreads][4];
-  __shared__ uint8_t s_mask[kThreads];
-  __shared__ uint32_t s_ridx[kThreads];
-  __shared__ uint32_t s_wmax[kThreads / 32];
+template <int TW, int TH, int S, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts ro,
+                                                       const float4* __restrict__ rec,
+                                                       const uint32_t* __restrict__ vals,
+                                                       const uint32_t* __restrict__ ranges,
+                                                       const float* __restrict__ Tfin,
+                                                       const uint32_t* __restrict__ ncontrib,
+                                                       const float* __restrict__ dLdC,
+                                                       float* __restrict__ grad2d,
+                                                       const int32_t* __restrict__ status,
+                                                       uint32_t* ctr, const uint32_t* __restrict__ order) {
+  constexpr int NT = TW * TH, NW = NT / 32, BXW = TW / 8;
+  __shared__ float4 s_rec[S][4];
+  __shared__ uint32_t s_mask[S];
+  __shared__ uint32_t s_ridx[S];
+  __shared__ uint32_t s_wmax[NW];
+  __shared__ int s_item;
   if (*status != 0) return;
-  const int g = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int v = view_of_tile(vt, g);
-  const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
-  const int lt = g - vt.v[v].tile_off;
-  const int ty = lt / ntx, tx = lt - ty * ntx;
-  const int x = tx * 16 + (warp & 1) * 8 + (lane & 7);
-  const int y = ty * 16 + (warp >> 1) * 4 + (lane >> 3);
-  const bool inside = x < W && y < H;
-  const float xf = (float)x, yf = (float)y;
-  const float tx0f = (float)(tx * 16), ty0f = (float)(ty * 16);
-  const uint32_t start = ranges[g];
   const float amax = ro.alpha_max;
   const int my_field = warp_sum10_field(lane);
+  for (int iter = 0;; ++iter) {
+    const int g = next_tile<PERSIST>(iter, vt.total_tiles, ctr, order, &s_item);
+    if (g < 0) break;
+    const int v = view_of_tile(vt, g);
+    const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
+    const int lt = g - vt.v[v].tile_off;
+    const int ty = lt / ntx, tx = lt - ty * ntx;
+    const int x = tx * TW + (warp % BXW) * 8 + (lane & 7);
+    const int y = ty * TH + (warp / BXW) * 4 + (lane >> 3);
+    const bool inside = x < W && y < H;
+    const float xf = (float)x, yf = (float)y;
+    const float tx0f = (float)(tx * TW), ty0f = (float)(ty * TH);
+    const uint32_t start = ranges[g];
 
-  float T = 1.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, GS = 0.0f;
-  uint32_t nl = 0;
-  if (inside) {
-    const int64_t HW = (int64_t)W * H;
-    const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
-    const float* gb = dLdC + 3 * vt.v[v].pix_off + (int64_t)y * W + x;
-    gx = gb[0];
-    gy = gb[HW];
-    gz = gb[2 * HW];
-    T = Tfin[pix];
-    nl = ncontrib[pix];
-    GS = T * (gx * vt.v[v].bg[0] + gy * vt.v[v].bg[1] + gz * vt.v[v].bg[2]);
-  }
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, nl);
-  if (lane == 0) s_wmax[warp] = wmax;
-  __syncthreads();
-  uint32_t bmax = 0;
-#pragma unroll
-  for (int w = 0; w < kThreads / 32; ++w) bmax = max(bmax, s_wmax[w]);
-
-  for (int top = (int)bmax; top > 0; top -= kThreads) {
-    const int lo = max(0, top - kThreads);
-    const int cnt = top - lo;
-    __syncthreads();
-    if (tid < cnt) {
-      const uint32_t r = vals[start + lo + tid];
-      const float4 f0 = rec[(size_t)r * 4 + 0];
-      const float4 f1 = rec[(size_t)r * 4 + 1];
-      const float4 f2 = rec[(size_t)r * 4 + 2];
-      const float4 f3 = rec[(size_t)r * 4 + 3];
-      s_rec[tid][0] = f0;
-      s_rec[tid][1] = f1;
-      s_rec[tid][2] = f2;
-      s_rec[tid][3] = f3;
-      s_mask[tid] = warp_mask(f0, f1, f3, tx0f, ty0f);
-      s_ridx[tid] = r;
+    float T = 1.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, GS = 0.0f;
+    uint32_t nl = 0;
+    if (inside) {
+      const int64_t HW = (int64_t)W * H;
+      const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
+      const float* gb = dLdC + 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+      gx = gb[0];
+      gy = gb[HW];
+      gz = gb[2 * HW];
+      T = Tfin[pix];
+      nl = ncontrib[pix];
+      GS = T * (gx * vt.v[v].bg[0] + gy * vt.v[v].bg[1] + gz * vt.v[v].bg[2]);
     }
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, nl);
+    if (lane == 0) s_wmax[warp] = wmax;
     __syncthreads();
-    for (int c = ((cnt - 1) >> 5) << 5; c >= 0; c -= 32) {
-      if ((uint32_t)(lo + c) >= wmax) continue;
-      const int idx = c + lane;
-      const bool bit = idx < cnt && ((s_mask[idx] >> warp) & 1u) && (uint32_t)(lo + idx) < wmax;
-      uint32_t bits = __ballot_sync(0xffffffffu, bit);
-      while (bits) {
-        const int k = 31 - __clz(bits);
-        bits &= ~(1u << k);
-        const int s = c + k;
-        const uint32_t pos = (uint32_t)(lo + s);
-        const float4 f0 = s_rec[s][0];
-        const float4 f1 = s_rec[s][1];
-        const float dx = (xf - f0.x) + f0.z;
-        const float dy = (yf - f0.y) + f0.w;
-        const float u = f1.x * dx;
-        const float vv = fmaf(f1.z, dx, f1.y * dy);
-        const float r2 = fmaf(u, u, vv * vv);
-        const bool act = pos < nl && r2 < 1.0f;
-        const uint32_t amask = __ballot_sync(0xffffffffu, act);
-        if (amask == 0u) continue;
-        float G[kGrad2d];
+    uint32_t bmax = 0;
 #pragma unroll
-        for (int q = 0; q < kGrad2d; ++q) G[q] = 0.0f;
-        if (act) {
-          const float4 f2 = s_rec[s][2];
-          const float4 f3 = s_rec[s][3];
-          const float beta = f1.w, inv_o = f3.z;
-          const float base = 1.0f - r2;
-          const float lb = lg2_approx(base);
-          const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
-          const float a = fminf(a0, amax);
-          const float inv = rcp_approx(1.0f - a);
-          const float Tk = T * inv;
-          const float gc = fmaf(gx, f2.y, fmaf(gy, f2.z, gz * f2.w));
-          const float dLa = fmaf(Tk, gc, -GS * inv);
-          const float wgt = a * Tk;
-          GS = fmaf(wgt, gc, GS);
-          G[7] = wgt * gx;
-          G[8] = wgt * gy;
-          G[9] = wgt * gz;
-          if (a0 < amax) {
-            const float t = dLa * a0;
-            G[5] = a0 > 0.0f ? t * inv_o : 0.0f;              // d o     (B = alpha / o)
-            G[6] = t * lb * 0.6931471805599453f;              // d beta  (alpha ln(1 - r^2))
-            const float dr2 = -t * beta * rcp_approx(base);   // dL/dr^2
-            const float w0 = fmaf(f1.x, u, f1.z * vv);        // Sigma'^-1 d
-            const float w1 = f1.y * vv;
-            const float m2 = -2.0f * dr2;
-            G[0] = m2 * w0;                                   // d mu'_x
-            G[1] = m2 * w1;                                   // d mu'_y
-            G[2] = -dr2 * w0 * w0;                            // d Sigma'_xx
-            G[3] = m2 * w0 * w1;                              // d Sigma'_xy
-            G[4] = -dr2 * w1 * w1;                            // d Sigma'_yy
-          }
-          T = Tk;
-        }
-        float* gdst = grad2d + (size_t)s_ridx[s] * kGrad2d;
-        if (__popc(amask) <= 2) {
-          // few lanes: direct atomics beat the cross-lane reduction
+    for (int w = 0; w < NW; ++w) bmax = max(bmax, s_wmax[w]);
+
+    for (int top = (int)bmax; top > 0; top -= S) {
+      const int lo = max(0, top - S);
+      const int cnt = top - lo;
+      __syncthreads();
+      for (int jj = tid; jj < cnt; jj += NT) {
+        const uint32_t r = vals[start + lo + jj];
+        const float4 f0 = rec[(size_t)r * 4 + 0];
+        const float4 f1 = rec[(size_t)r * 4 + 1];
+        const float4 f2 = rec[(size_t)r * 4 + 2];
+        const float4 f3 = rec[(size_t)r * 4 + 3];
+        s_rec[jj][0] = f0;
+        s_rec[jj][1] = f1;
+        s_rec[jj][2] = f2;
+        s_rec[jj][3] = f3;
+        s_mask[jj] = warp_mask<TW, TH>(f0, f1, f3, tx0f, ty0f);
+        s_ridx[jj] = r;
+      }
+      __syncthreads();
+      for (int c = ((cnt - 1) >> 5) << 5; c >= 0; c -= 32) {
+        if ((uint32_t)(lo + c) >= wmax) continue;
+        const int idx = c + lane;
+        const bool bit = idx < cnt && ((s_mask[idx] >> warp) & 1u) && (uint32_t)(lo + idx) < wmax;
+        uint32_t bits = __ballot_sync(0xffffffffu, bit);
+        while (bits) {
+          const int k = 31 - __clz(bits);
+          bits &= ~(1u << k);
+          const int s = c + k;
+          const uint32_t pos = (uint32_t)(lo + s);
+          const float4 f0 = s_rec[s][0];
+          const float4 f1 = s_rec[s][1];
+          const float dx = (xf - f0.x) + f0.z;
+          const float dy = (yf - f0.y) + f0.w;
+          const float u = f1.x * dx;
+          const float vv = fmaf(f1.z, dx, f1.y * dy);
+          const float r2 = fmaf(u, u, vv * vv);
+          const bool act = pos < nl && r2 < 1.0f;
+          const uint32_t amask = __ballot_sync(0xffffffffu, act);
+          if (amask == 0u) continue;
+          float G[kGrad2d];
+#pragma unroll
+          for (int q = 0; q < kGrad2d; ++q) G[q] = 0.0f;
           if (act) {
-#pragma unroll
-            for (int q = 0; q < kGrad2d; ++q)
-              if (G[q] != 0.0f) atomicAdd(gdst + q, G[q]);
+            const float4 f2 = s_rec[s][2];
+            const float4 f3 = s_rec[s][3];
+            const float beta = f1.w, inv_o = f3.z;
+            const float base = 1.0f - r2;
+            const float lb = lg2_approx(base);
+            const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
+            const float a = fminf(a0, amax);
+            const float inv = rcp_approx(1.0f - a);
+            const float Tk = T * inv;
+            const float gc = fmaf(gx, f2.y, fmaf(gy, f2.z, gz * f2.w));
+            const float dLa = fmaf(Tk, gc, -GS * inv);
+            const float wgt = a * Tk;
+            GS = fmaf(wgt, gc, GS);
+            G[7] = wgt * gx;
+            G[8] = wgt * gy;
+            G[9] = wgt * gz;
+            if (a0 < amax) {
+              const float t = dLa * a0;
+              G[5] = a0 > 0.0f ? t * inv_o : 0.0f;              // d o     (B = alpha / o)
+              G[6] = t * lb * 0.6931471805599453f;              // d beta  (alpha ln(1 - r^2))
+              const float dr2 = -t * beta * rcp_approx(base);   // dL/dr^2
+              const float w0 = fmaf(f1.x, u, f1.z * vv);        // Sigma'^-1 d
+              const float w1 = f1.y * vv;
+              const float m2 = -2.0f * dr2;
+              G[0] = m2 * w0;                                   // d mu'_x
+              G[1] = m2 * w1;                                   // d mu'_y
+              G[2] = -dr2 * w0 * w0;                            // d Sigma'_xx
+              G[3] = m2 * w0 * w1;                              // d Sigma'_xy
+              G[4] = -dr2 * w1 * w1;                            // d Sigma'_yy
+            }
+            T = Tk;
           }
-        } else {
-          const float tot = warp_sum10(G, lane);
-          if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
+          float* gdst = grad2d + (size_t)s_ridx[s] * kGrad2d;
+          if (__popc(amask) <= 2) {
+            // few lanes: direct atomics beat the cross-lane reduction
+            if (act) {
+#pragma unroll
+              for (int q = 0; q < kGrad2d; ++q)
+                if (G[q] != 0.0f) atomicAdd(gdst + q, G[q]);
+            }
+          } else {
+            const float tot = warp_sum10(G, lane);
+            if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
+          }
         }
       }
     }
+    __syncthreads();
+  }
+  leave<PERSIST>(ctr);
+}
+
+// ---------------------------------------------------------------------------
+// longest-first schedule: bucket b = bit length of the tile's pair count,
+// buckets emitted from the longest down (order inside a bucket is arbitrary:
+// the result of a tile does not depend on when it runs).
+// layout (u32): [0..1] forward counter, [2..3] backward counter, [16..79]
+// bucket counts, [80..143] bucket cursors, [144..] order.
+// ---------------------------------------------------------------------------
+constexpr int kSchedHist = 16, kSchedCursor = 80, kSchedOrder = 144, kBuckets = 33;
+
+__device__ __forceinline__ int tile_bucket(uint32_t count) {
+  return count == 0u ? 0 : 32 - __clz(count);
+}
+
+__global__ void k_sched_prep(uint32_t* sched) {
+  for (int i = threadIdx.x; i < kSchedOrder; i += blockDim.x) sched[i] = 0u;
+}
+
+__global__ void k_sched_hist(const uint32_t* __restrict__ ranges, int total_tiles, uint32_t* sched,
+                             const int32_t* __restrict__ status) {
+  __shared__ uint32_t h[kBuckets];
+  if (*status != 0) return;
+  for (int i = threadIdx.x; i < kBuckets; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total_tiles; g += gridDim.x * blockDim.x)
+    atomicAdd(&h[tile_bucket(ranges[g + 1] - ranges[g])], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kBuckets; i += blockDim.x)
+    if (h[i]) atomicAdd(&sched[kSchedHist + i], h[i]);
+}
+
+__global__ void k_sched_scatter(const uint32_t* __restrict__ ranges, int total_tiles,
+                                uint32_t* sched, const int32_t* __restrict__ status) {
+  __shared__ uint32_t base[kBuckets];
+  if (*status != 0) return;
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int b = kBuckets - 1; b >= 0; --b) {
+      base[b] = run;
+      run += sched[kSchedHist + b];
+    }
+  }
+  __syncthreads();
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total_tiles; g += gridDim.x * blockDim.x) {
+    const int b = tile_bucket(ranges[g + 1] - ranges[g]);
+    const uint32_t pos = base[b] + atomicAdd(&sched[kSchedCursor + b], 1u);
+    sched[kSchedOrder + pos] = (uint32_t)g;
   }
 }
 
@@ -413,24 +512,112 @@ __global__ void k_l1_reduce(ViewTable vt, const float* __restrict__ partial, int
 
 }  // namespace
 
+size_t schedule_bytes(int total_tiles) { return (size_t)(kSchedOrder + total_tiles) * 4; }
+
+cudaError_t launch_schedule(const ViewTable& vt, const uint32_t* ranges, uint32_t* sched,
+                            const int32_t* status, cudaStream_t s) {
+  const int T = vt.total_tiles;
+  const int grid = std::max(1, std::min((T + 255) / 256, 152 * 4));
+  k_sched_prep<<<1, 160, 0, s>>>(sched);
+  k_sched_hist<<<grid, 256, 0, s>>>(ranges, T, sched, status);
+  k_sched_scatter<<<grid, 256, 0, s>>>(ranges, T, sched, status);
+  return cudaGetLastError();
+}
+
+namespace {
+
+int g_sms = 0;
+int sms() {
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+template <typename K>
+int persistent_grid(K kernel, int threads, int total_tiles) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return std::max(1, std::min(total_tiles, per_sm * sms()));
+}
+
+template <int TW, int TH, int S>
+cudaError_t fwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
+                      const uint32_t* vals, const uint32_t* ranges, float* color, float* T_final,
+                      uint32_t* n_contrib, const int32_t* status, uint32_t* sched, cudaStream_t s) {
+  if (sched) {
+    auto k = k_raster_fwd<TW, TH, S, true>;
+    k<<<persistent_grid(k, TW * TH, vt.total_tiles), TW * TH, 0, s>>>(
+        vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched + 0, sched + kSchedOrder);
+  } else {
+    k_raster_fwd<TW, TH, S, false><<<vt.total_tiles, TW * TH, 0, s>>>(
+        vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, nullptr, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+template <int TW, int TH, int S>
+cudaError_t bwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
+                      const uint32_t* vals, const uint32_t* ranges, const float* T_final,
+                      const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
+                      const int32_t* status, uint32_t* sched, cudaStream_t s) {
+  if (sched) {
+    auto k = k_raster_bwd<TW, TH, S, true>;
+    k<<<persistent_grid(k, TW * TH, vt.total_tiles), TW * TH, 0, s>>>(
+        vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, sched + 2,
+        sched + kSchedOrder);
+  } else {
+    k_raster_bwd<TW, TH, S, false><<<vt.total_tiles, TW * TH, 0, s>>>(
+        vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, nullptr, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+// (tile shape, batch) -> instantiation.  Supported: 8x8, 16x8, 16x16, 32x16
+// tiles; batches of 64, 128 or 256 records (at most 4 records per thread).
+#define BETA_TILE_DISPATCH(FN, ...)                                                 \
+  switch (ro.tile_w * 1000 + ro.tile_h) {                                           \
+    case 8008:                                                                      \
+      if (ro.batch_s == 64) return FN<8, 8, 64>(__VA_ARGS__);                       \
+      if (ro.batch_s == 128) return FN<8, 8, 128>(__VA_ARGS__);                     \
+      return FN<8, 8, 256>(__VA_ARGS__);                                            \
+    case 16008:                                                                     \
+      if (ro.batch_s == 64) return FN<16, 8, 64>(__VA_ARGS__);                      \
+      if (ro.batch_s == 128) return FN<16, 8, 128>(__VA_ARGS__);                    \
+      return FN<16, 8, 256>(__VA_ARGS__);                                           \
+    case 16016:                                                                     \
+      if (ro.batch_s == 64) return FN<16, 16, 64>(__VA_ARGS__);                     \
+      if (ro.batch_s == 128) return FN<16, 16, 128>(__VA_ARGS__);                   \
+      return FN<16, 16, 256>(__VA_ARGS__);                                          \
+    case 32016:                                                                     \
+      if (ro.batch_s == 64) return FN<32, 16, 64>(__VA_ARGS__);                     \
+      if (ro.batch_s == 128) return FN<32, 16, 128>(__VA_ARGS__);                   \
+      return FN<32, 16, 256>(__VA_ARGS__);                                          \
+    default:                                                                        \
+      return cudaErrorInvalidValue;                                                 \
+  }
+
+}  // namespace
+
 cudaError_t launch_raster_fwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                               const uint32_t* vals, const uint32_t* ranges, float* color,
                               float* T_final, uint32_t* n_contrib, const int32_t* status,
-                              cudaStream_t s) {
+                              uint32_t* sched, cudaStream_t s) {
   if (vt.total_tiles <= 0) return cudaSuccess;
-  k_raster_fwd<<<vt.total_tiles, kThreads, 0, s>>>(vt, ro, rec, vals, ranges, color, T_final,
-                                                   n_contrib, status);
-  return cudaGetLastError();
+  BETA_TILE_DISPATCH(fwd_shape, vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched, s)
 }
 
 cudaError_t launch_raster_bwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                               const uint32_t* vals, const uint32_t* ranges, const float* T_final,
                               const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
-                              const int32_t* status, cudaStream_t s) {
+                              const int32_t* status, uint32_t* sched, cudaStream_t s) {
   if (vt.total_tiles <= 0) return cudaSuccess;
-  k_raster_bwd<<<vt.total_tiles, kThreads, 0, s>>>(vt, ro, rec, vals, ranges, T_final, n_contrib,
-                                                   dL_dcolor, grad2d, status);
-  return cudaGetLastError();
+  BETA_TILE_DISPATCH(bwd_shape, vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d,
+                     status, sched, s)
 }
 
 // the L1 block offsets of each view ride in ViewDev::pad0

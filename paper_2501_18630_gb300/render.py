@@ -27,7 +27,7 @@ class Rasterizer:
     forward overwrites the saved per-pixel state of the first."""
 
     def __init__(self, n, pitch, n_lobes, cameras, opts: _lib.BetaOpts | None = None,
-                 pair_capacity: int | None = None, device="cuda"):
+                 pair_capacity: int | None = None, device="cuda", persistent: bool = False):
         self.L = _lib.load()
         self.n, self.pitch, self.n_lobes = int(n), int(pitch), int(n_lobes)
         self.cameras = list(cameras)
@@ -60,6 +60,11 @@ class Rasterizer:
         self.l1_ws = torch.empty(max(4, int(L.beta_l1_workspace_bytes(self.cams, self.V))), dtype=torch.uint8, device=dev)
         cap = pair_capacity if pair_capacity is not None else max(1 << 16, 4 * self.n * self.V)
         self._alloc_pairs(cap)
+        self.persistent = bool(persistent)
+        self.sched = None
+        if self.persistent:
+            nb = int(L.beta_schedule_bytes(self.cams, self.V, ctypes.byref(self.opts)))
+            self.sched = torch.zeros(nb // 4, dtype=torch.int32, device=dev)
 
     # -- buffers -----------------------------------------------------------
     def _alloc_pairs(self, cap: int):
@@ -98,12 +103,18 @@ class Rasterizer:
             _vp(self.pair_vals), self.cap, _vp(self.ranges), _vp(self.count), _vp(self.status),
             _vp(self.sort_ws), self.sort_ws.numel(), _stream()))
 
+    def schedule(self):
+        """Longest-first tile order for the persistent raster kernels."""
+        _lib.check("beta_schedule", self.L.beta_schedule(
+            self.cams, self.V, ctypes.byref(self.opts), _vp(self.ranges), _vp(self.sched),
+            _vp(self.status), _stream()))
+
     def raster_fwd(self, planes):
         prm = self.params(planes)
         _lib.check("beta_raster_fwd", self.L.beta_raster_fwd(
             ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
-            _vp(self.pair_vals), _vp(self.ranges), _vp(self.color), _vp(self.T_final),
-            _vp(self.n_contrib), _vp(self.status), _stream()))
+            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), _vp(self.color),
+            _vp(self.T_final), _vp(self.n_contrib), _vp(self.status), _stream()))
 
     def l1_loss(self, target: torch.Tensor):
         assert target.numel() == self.color.numel() and target.is_contiguous()
@@ -117,8 +128,8 @@ class Rasterizer:
         assert dL_dcolor.numel() == self.color.numel() and dL_dcolor.is_contiguous()
         _lib.check("beta_raster_bwd", self.L.beta_raster_bwd(
             ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
-            _vp(self.pair_vals), _vp(self.ranges), _vp(self.T_final), _vp(self.n_contrib),
-            _vp(dL_dcolor), _vp(self.grad2d), _vp(self.status), _stream()))
+            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), _vp(self.T_final),
+            _vp(self.n_contrib), _vp(dL_dcolor), _vp(self.grad2d), _vp(self.status), _stream()))
 
     def project_bwd(self, planes, grad_planes):
         prm = self.params(planes)
@@ -146,6 +157,8 @@ class Rasterizer:
                 st, k = self.device_status()
             if st != _lib.BETA_OK:
                 raise _lib.BetaError("beta_bin_sort", st, self.L.beta_status_string(st).decode())
+        if self.persistent:
+            self.schedule()
         self.raster_fwd(planes)
         return self.color
 
