@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip per-view, e2e and CPU legs (profiling runs)")
     ap.add_argument("--cpu-pixels", type=int, default=16384)
+    ap.add_argument("--config", default=None,
+                    help="pin the raster configuration instead of autotuning, e.g. 16x16/256/P (P persistent, G one CTA per tile)")
     return ap.parse_args()
 
 
@@ -225,8 +227,13 @@ def main():
     # ---- autotuned batched step, captured as one CUDA graph -----------------
     from paper_2501_18630_gb300 import autotune, batched
     t_tune = time.perf_counter()
-    best, tune_ms = autotune.tune(planes, sc.n, sc.n_lobes, cams, target, reps=3,
-                                  log=(lambda m: print(m, file=sys.stderr)) if rank == 0 else None)
+    if args.config:
+        shape, bsz, mode = args.config.split("/")
+        tw_, th_ = (int(x) for x in shape.split("x"))
+        best, tune_ms = (tw_, th_, int(bsz), mode.upper() == "P"), {}
+    else:
+        best, tune_ms = autotune.tune(planes, sc.n, sc.n_lobes, cams, target, reps=3,
+                                      log=(lambda m: print(m, file=sys.stderr)) if rank == 0 else None)
     t_tune = time.perf_counter() - t_tune
     tw, th, bs, persist = best
     opts = _lib.default_opts(tile_w=tw, tile_h=th, batch_s=bs)

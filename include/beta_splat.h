@@ -213,9 +213,12 @@ int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color,
                  beta_stream_t stream);
 
 /* Step 4a (backward of Eq. C): walks each pixel's list from its last
- * contributor down, recovering T by division, and accumulates per-record 2D
- * gradients (d mu' (2), d Sigma' (a, b, c), d o, d beta, d colour (3)) with
- * warp-reduced atomics into grad2d.
+ * contributor down, recovering T by division, and accumulates ten per-record
+ * sums with warp-reduced atomics into grad2d: in whitened coordinates
+ * (u, v) = L^-1 (x - mu') (Sigma' = L L^T) and with k = (dL/dalpha) alpha /
+ * (1 - r^2) -- sum k (u, v, u^2, u v, v^2), sum (dL/dalpha) alpha, the same
+ * times log2(1 - r^2), and sum alpha T dL/dC (3).  beta_project_bwd turns
+ * them into d mu', d Sigma', d o, d beta and d colour.
  *   sched     beta_schedule() output (persistent launch) or NULL
  *   dL_dcolor [3 x total_pixels] in (layout of color)
  *   grad2d    [beta_grad2d_bytes()] in/out: 10 floats per record, ACCUMULATED.

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
 // first and taken through the view-independent maps once.
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ planes, int n,
+__global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict__ planes, int n,
                                                      int pitch, ViewTable vt, RenderOpts ro,
                                                      float* __restrict__ grad2d,
                                                      float* __restrict__ gout,
@@ -241,7 +241,28 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
       int rc[4];
       uint32_t kk;
       if (!rule_depth(pg, V, g, kk) || !rule_view(pg, V, ro.blur_eps, ro.tile_w, ro.tile_h, g, rc)) continue;
-      const float gmx = G[0], gmy = G[1], ga = G[2], gb = G[3], gc = G[4];
+      // whitening of Sigma' (the forward's formulas) turns the whitened sums
+      // into d mu' and d Sigma' = [[ga, gb/2], [gb/2, gc]] (gb: off-diagonal scalar)
+      float gmx, gmy, ga, gb, gc;
+      {
+        const float a0 = fmaf(g.M0[0], g.M0[0], fmaf(g.M0[1], g.M0[1], g.M0[2] * g.M0[2]));
+        const float c0 = fmaf(g.M1[0], g.M1[0], fmaf(g.M1[1], g.M1[1], g.M1[2] * g.M1[2]));
+        const float bb = fmaf(g.M0[0], g.M1[0], fmaf(g.M0[1], g.M1[1], g.M0[2] * g.M1[2]));
+        const float m01 = diff_of_products(g.M0[0], g.M1[1], g.M0[1], g.M1[0]);
+        const float m02 = diff_of_products(g.M0[0], g.M1[2], g.M0[2], g.M1[0]);
+        const float m12 = diff_of_products(g.M0[1], g.M1[2], g.M0[2], g.M1[1]);
+        float det = fmaf(m01, m01, fmaf(m02, m02, m12 * m12));
+        const float aa = a0 + ro.blur_eps;
+        if (ro.blur_eps != 0.0f) det = fmaf(ro.blur_eps, a0 + c0 + ro.blur_eps, det);
+        const float sa = sqrtf(aa), sd = sqrtf(det);
+        const float p = 1.0f / sa, q1 = sa / sd, q2 = -(bb * p) / sd;
+        const float b2 = 2.0f * at.beta;
+        gmx = b2 * fmaf(p, G[0], q2 * G[1]);
+        gmy = b2 * q1 * G[1];
+        ga = at.beta * fmaf(p * p, G[2], fmaf(2.0f * p * q2, G[3], q2 * q2 * G[4]));
+        gb = b2 * q1 * fmaf(p, G[3], q2 * G[4]);
+        gc = at.beta * q1 * q1 * G[4];
+      }
       // Sigma' = M M^T: dM0 = 2 ga M0 + gb M1, dM1 = gb M0 + 2 gc M1
       float dM0[3], dM1[3];
 #pragma unroll
@@ -282,8 +303,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
       gp[0] += V.R[0] * dtx + V.R[3] * dty + V.R[6] * dtz;
       gp[1] += V.R[1] * dtx + V.R[4] * dty + V.R[7] * dtz;
       gp[2] += V.R[2] * dtx + V.R[5] * dty + V.R[8] * dtz;
-      go += G[5];
-      gbeta += G[6];
+      go += G[5];                               // times 1/o below
+      gbeta += G[6];                            // times ln 2 below
       // colour
       const float gr = G[7], gg = G[8], gbl = G[9];
       if (ro.color_mode != 2) {
@@ -348,8 +369,10 @@ __global__ void __launch_bounds__(256) k_project_bwd(const float* __restrict__ p
     gp[8] = (dy - y * qd) * iq;
     gp[9] = (dz - z * qd) * iq;
     // opacity logit and shape
-    gp[10] = go * at.o * (1.0f - at.o);
-    gp[11] = gbeta * at.beta;
+    // dL/do = (1/o) sum (dL/dalpha) alpha; sigmoid' = o (1 - o)
+    gp[10] = go * (1.0f - at.o);
+    // dL/dbeta = ln 2 sum (dL/dalpha) alpha log2(1 - r^2); dbeta/db = beta
+    gp[11] = gbeta * kLn2 * at.beta;
     // lobe directions R = (sin t cos p, sin t sin p, cos t)
 #pragma unroll
     for (int m = 0; m < M; ++m) {

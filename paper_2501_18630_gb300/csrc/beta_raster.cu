@@ -348,13 +348,17 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
           const bool act = pos < nl && r2 < 1.0f;
           const uint32_t amask = __ballot_sync(0xffffffffu, act);
           if (amask == 0u) continue;
+          // Per-lane terms of the record's 2D gradients, in whitened coordinates
+          // (u, v) = L^-1 (x - mu'); beta, 1/o, ln 2 and the whitening matrix are
+          // per-record constants applied by the projection backward:
+          //   G0..G4 = k (u, v, u^2, u v, v^2),  k = (dL/dalpha) alpha / (1 - r^2)
+          //   G5 = (dL/dalpha) alpha,  G6 = G5 log2(1 - r^2),  G7..9 = alpha T dL/dC
           float G[kGrad2d];
 #pragma unroll
           for (int q = 0; q < kGrad2d; ++q) G[q] = 0.0f;
           if (act) {
             const float4 f2 = s_rec[s][2];
-            const float4 f3 = s_rec[s][3];
-            const float beta = f1.w, inv_o = f3.z;
+            const float beta = f1.w;
             const float base = 1.0f - r2;
             const float lb = lg2_approx(base);
             const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
@@ -368,20 +372,15 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
             G[7] = wgt * gx;
             G[8] = wgt * gy;
             G[9] = wgt * gz;
-            if (a0 < amax) {
-              const float t = dLa * a0;
-              G[5] = a0 > 0.0f ? t * inv_o : 0.0f;              // d o     (B = alpha / o)
-              G[6] = t * lb * 0.6931471805599453f;              // d beta  (alpha ln(1 - r^2))
-              const float dr2 = -t * beta * rcp_approx(base);   // dL/dr^2
-              const float w0 = fmaf(f1.x, u, f1.z * vv);        // Sigma'^-1 d
-              const float w1 = f1.y * vv;
-              const float m2 = -2.0f * dr2;
-              G[0] = m2 * w0;                                   // d mu'_x
-              G[1] = m2 * w1;                                   // d mu'_y
-              G[2] = -dr2 * w0 * w0;                            // d Sigma'_xx
-              G[3] = m2 * w0 * w1;                              // d Sigma'_xy
-              G[4] = -dr2 * w1 * w1;                            // d Sigma'_yy
-            }
+            const float t = a0 < amax ? dLa * a0 : 0.0f;         // clamped alpha: no o/beta/r^2 gradient
+            const float kk = t * rcp_approx(base);
+            G[0] = kk * u;
+            G[1] = kk * vv;
+            G[2] = G[0] * u;
+            G[3] = G[0] * vv;
+            G[4] = G[1] * vv;
+            G[5] = t;
+            G[6] = t * lb;
             T = Tk;
           }
           float* gdst = grad2d + (size_t)s_ridx[s] * kGrad2d;
