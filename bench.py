@@ -46,12 +46,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--views", type=int, default=16)
-    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--n", type=int, default=None, help="Betas (default: the workload's, 1M for workload 3)")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip per-view, e2e and CPU legs (profiling runs)")
     ap.add_argument("--cpu-pixels", type=int, default=16384)
+    ap.add_argument("--workload", type=int, default=3, choices=[3, 4, 5],
+                    help="scene recipe: 3 = 1M Betas (default), 4 = 3M Betas, 5 = 6M Betas")
     ap.add_argument("--config", default=None,
                     help="pin the raster configuration instead of autotuning, e.g. 16x16/256/P (P persistent, G one CTA per tile)")
     return ap.parse_args()
@@ -170,7 +172,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2501_18630_gb300 import scenes
-    sc = scenes.config_scene(3, n=args.n, n_views=args.views)
+    sc = scenes.config_scene(args.workload, n=args.n, n_views=args.views)
     cams = scenes.ring_cameras(args.views, 4.0, 15.0, (args.width, args.height))
     px = 1024
     value, cores, total = oracle_leg(args, cams, sc, px, args.steps, args.warmup)
@@ -179,9 +181,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.n} Betas (256 sheets, 3 SB lobes), {args.views} views "
+        "config": {"workload": f"{sc.n} Betas (256 sheets, 3 SB lobes), {args.views} views "
                                f"{args.width}x{args.height}; FP64 oracle forward on {px} sampled pixels per step",
-                   "n_betas": args.n, "views": args.views},
+                   "n_betas": sc.n, "views": args.views},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{px} seeded pixels of one view per step, forward only (the oracle has no backward)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -203,7 +205,7 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2501_18630_gb300 import _lib, render, scenes
+    from paper_2501_18630_gb300 import _lib, distributed, render, scenes
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -216,9 +218,9 @@ def main():
     _lib.load()
 
     V = args.views
-    sc = scenes.config_scene(3, n=args.n, n_views=V)
+    sc = scenes.config_scene(args.workload, n=args.n, n_views=V)
     ring = scenes.ring_cameras(V * world, 4.0, 15.0, (args.width, args.height))
-    cams = ring[rank::world]
+    cams = distributed.shard_views(ring, rank, world)
     planes = torch.from_numpy(sc.planes).to(dev)
     targets_np = scenes.target_images(cams, seed=77 + rank)
     target = torch.from_numpy(np.concatenate([t.reshape(-1) for t in targets_np])).to(dev)
@@ -243,8 +245,7 @@ def main():
 
     def step():
         bstep.step()
-        if world > 1:
-            dist.all_reduce(grad)
+        distributed.reduce_gradients(grad)
 
     stream = torch.cuda.current_stream()
 
@@ -254,11 +255,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return distributed.max_over_ranks(x, dev)
 
     for _ in range(args.warmup):
         step()
@@ -405,13 +402,13 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{args.n} Betas (256 planar sheets, 3 SB lobes), {V} views {args.width}x{args.height} "
+        "config": {"workload": f"{sc.n} Betas (256 planar sheets, 3 SB lobes), {V} views {args.width}x{args.height} "
                                f"per GPU, fwd+bwd with per-view L1 loss, one CUDA-graph replay per step",
                    "tile": f"{tw}x{th}", "batch_s": bs, "persistent": persist,
                    "autotune": {"s": round(t_tune, 1), "ms": {f"{c[0]}x{c[1]}/S{c[2]}/{'P' if c[3] else 'G'}": round(v, 3)
                                                               for c, v in tune_ms.items()}},
-                   "n_betas": args.n, "views_per_gpu": V, "resolution": f"{args.width}x{args.height}",
-                   "pairs_per_step": K, "l2": f"inputs larger than L2: {args.n * n_planes * 4 / 1e6:.0f} MB params + "
+                   "n_betas": sc.n, "views_per_gpu": V, "resolution": f"{args.width}x{args.height}",
+                   "pairs_per_step": K, "l2": f"inputs larger than L2: {sc.n * n_planes * 4 / 1e6:.0f} MB params + "
                                                f"{V * sc.pitch * 76 / 1e6:.0f} MB records per step",
                    "parallelism": f"dp{world} over views"},
         "ms_per_view": ms_step / V,

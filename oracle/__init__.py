@@ -55,7 +55,7 @@ class OCam(ctypes.Structure):
 class OOpts(ctypes.Structure):
     _fields_ = [("t_eps", ctypes.c_double), ("alpha_max", ctypes.c_double),
                 ("blur_eps", ctypes.c_double), ("color_mode", ctypes.c_int32),
-                ("n_threads", ctypes.c_int32)]
+                ("n_threads", ctypes.c_int32), ("b_lo", ctypes.c_double), ("b_hi", ctypes.c_double)]
 
 
 class OPrim(ctypes.Structure):
@@ -84,8 +84,8 @@ def lib():
             L.oracle_rule_exp.argtypes = [ctypes.c_float]
             L.oracle_rule_rects.restype = None
             L.oracle_rule_rects.argtypes = [fp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                            ctypes.POINTER(OCam), ctypes.c_float, ctypes.c_int32,
-                                            ctypes.c_int32, ip, up, ip]
+                                            ctypes.POINTER(OCam), ctypes.c_float, ctypes.c_float,
+                                            ctypes.c_float, ctypes.c_int32, ctypes.c_int32, ip, up, ip]
             _lib = L
     return _lib
 
@@ -112,8 +112,10 @@ def make_cam(cam) -> OCam:
 
 
 def make_opts(t_eps=DEFAULT_T_EPS, alpha_max=DEFAULT_ALPHA_MAX, blur_eps=0.0, color_mode=0,
-              n_threads=None) -> OOpts:
+              n_threads=None, b_lo=-np.inf, b_hi=np.inf) -> OOpts:
     o = OOpts()
+    o.b_lo = float(np.float32(b_lo))
+    o.b_hi = float(np.float32(b_hi))
     o.t_eps = float(np.float32(t_eps))
     o.alpha_max = float(np.float32(alpha_max))
     o.blur_eps = float(np.float32(blur_eps))
@@ -177,8 +179,9 @@ def rule_exp(x: float) -> float:
     return float(lib().oracle_rule_exp(ctypes.c_float(x)))
 
 
-def rule_rects(planes, n, n_lobes, cam, blur_eps=0.0, tile_w=16, tile_h=16):
-    """Rule B1 rectangles (n,4) = (tx0, tx1, ty0, ty1), rule D keys (n,), binned flags (n,)."""
+def rule_rects(planes, n, n_lobes, cam, blur_eps=0.0, tile_w=16, tile_h=16, b_lo=-np.inf, b_hi=np.inf):
+    """Rule B1 rectangles (n,4) = (tx0, tx1, ty0, ty1), rule D keys (n,), binned flags (n,).
+    Primitives with b outside [b_lo, b_hi) are not binned (geometry decomposition)."""
     L = lib()
     p = np.ascontiguousarray(planes, dtype=np.float32)
     rects = np.zeros((max(n, 1), 4), np.int32)
@@ -186,7 +189,8 @@ def rule_rects(planes, n, n_lobes, cam, blur_eps=0.0, tile_w=16, tile_h=16):
     binned = np.zeros(max(n, 1), np.int32)
     oc = make_cam(cam)
     L.oracle_rule_rects(_ptr(p, ctypes.c_float), n, p.shape[1], n_lobes, ctypes.byref(oc),
-                        ctypes.c_float(np.float32(blur_eps)), tile_w, tile_h,
+                        ctypes.c_float(np.float32(blur_eps)), ctypes.c_float(np.float32(b_lo)),
+                        ctypes.c_float(np.float32(b_hi)), tile_w, tile_h,
                         _ptr(rects, ctypes.c_int32), _ptr(keys, ctypes.c_uint32),
                         _ptr(binned, ctypes.c_int32))
     return rects[:n], keys[:n], binned[:n]
@@ -196,7 +200,8 @@ def n_tiles(cam, tile_w=16, tile_h=16):
     return (cam.width + tile_w - 1) // tile_w, (cam.height + tile_h - 1) // tile_h
 
 
-def bin_pairs(planes, n, n_lobes, cams, blur_eps=0.0, tile_w=16, tile_h=16, pitch=None):
+def bin_pairs(planes, n, n_lobes, cams, blur_eps=0.0, tile_w=16, tile_h=16, pitch=None,
+              b_lo=-np.inf, b_hi=np.inf):
     """Sorted (global tile, record) pairs of a batch of views.
 
     A record is view * pitch + primitive.  Global tiles are numbered view by
@@ -208,7 +213,7 @@ def bin_pairs(planes, n, n_lobes, cams, blur_eps=0.0, tile_w=16, tile_h=16, pitc
     all_tiles, all_keys, all_rec = [], [], []
     tile_off = 0
     for v, cam in enumerate(cams):
-        rects, keys, binned = rule_rects(planes, n, n_lobes, cam, blur_eps, tile_w, tile_h)
+        rects, keys, binned = rule_rects(planes, n, n_lobes, cam, blur_eps, tile_w, tile_h, b_lo, b_hi)
         ntx, nty = n_tiles(cam, tile_w, tile_h)
         idx = np.nonzero(binned)[0]
         r = rects[idx].astype(np.int64)
@@ -254,7 +259,8 @@ def l1_loss(planes, n, n_lobes, cams, targets, pixel_sets=None, **opts):
 def support_pixels(planes, n, n_lobes, cam, i, margin=2.0, **opts):
     """Pixels whose centre lies inside the padded bounding box of primitive i's
     FP64 support ellipse (every pixel the primitive can touch)."""
-    pr = project(planes[:, :], n, n_lobes, cam, **{k: v for k, v in opts.items() if k in ("blur_eps", "color_mode")})
+    pr = project(planes[:, :], n, n_lobes, cam, **{k: v for k, v in opts.items()
+                                                   if k in ("blur_eps", "color_mode", "b_lo", "b_hi")})
     if not pr["valid"][i]:
         return np.zeros(0, np.int32), np.zeros(0, np.int32)
     a, _, c = pr["cov"][i]

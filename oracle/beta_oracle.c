@@ -53,6 +53,7 @@ typedef struct {
   double blur_eps;   /* added to the diagonal of Sigma'                   */
   int32_t color_mode;/* 0: c0 + lobes, 1: c0 only, 2: lobes only          */
   int32_t n_threads;
+  double b_lo, b_hi; /* geometry decomposition (Sec. 4.3): keep b_lo <= b < b_hi */
 } oopts;
 
 typedef struct {
@@ -118,6 +119,8 @@ void oracle_project_one(const double* planes, int32_t pitch, int32_t n_lobes, in
   const double* mu = p + 0;
   const double* ls = p + 3;
   const double* q = p + 6;
+  /* geometry decomposition by the Beta shape parameter (Sec. 4.3) */
+  if (!(p[11] >= op->b_lo && p[11] < op->b_hi)) return;
 
   /* rule D key and the near-plane cull (on the fp32 centre) */
   float tzf = rule_tz(cam, (float)mu[0], (float)mu[1], (float)mu[2]);
@@ -356,8 +359,8 @@ float oracle_rule_exp(float x) {
  * Returns 1 if the primitive is binned, 0 otherwise.  key receives the
  * rule D depth key. */
 int32_t oracle_rule_rect_one(const float* planes, int32_t pitch, int32_t n_lobes, int32_t i,
-                             const ocam* cam, float blur, int32_t tile_w, int32_t tile_h,
-                             int32_t rect[4], uint32_t* key) {
+                             const ocam* cam, float blur, float b_lo, float b_hi, int32_t tile_w,
+                             int32_t tile_h, int32_t rect[4], uint32_t* key) {
   rect[0] = 0;
   rect[1] = -1;
   rect[2] = 0;
@@ -368,6 +371,10 @@ int32_t oracle_rule_rect_one(const float* planes, int32_t pitch, int32_t n_lobes
       *key = 0xFFFFFFFFu;
       return 0;
     }
+  {
+    float bb = planes[11 * (size_t)pitch + i];
+    if (!(bb >= b_lo && bb < b_hi)) return 0;
+  }
   float mx = planes[0 * (size_t)pitch + i], my = planes[1 * (size_t)pitch + i], mz = planes[2 * (size_t)pitch + i];
   float W[9], tw[3];
   for (int k = 0; k < 9; ++k) W[k] = (float)cam->R[k];
@@ -473,9 +480,9 @@ int32_t oracle_rule_rect_one(const float* planes, int32_t pitch, int32_t n_lobes
 }
 
 void oracle_rule_rects(const float* planes, int32_t n, int32_t pitch, int32_t n_lobes,
-                       const ocam* cam, float blur, int32_t tile_w, int32_t tile_h,
-                       int32_t* rects, uint32_t* keys, int32_t* binned) {
+                       const ocam* cam, float blur, float b_lo, float b_hi, int32_t tile_w,
+                       int32_t tile_h, int32_t* rects, uint32_t* keys, int32_t* binned) {
   for (int32_t i = 0; i < n; ++i)
-    binned[i] = oracle_rule_rect_one(planes, pitch, n_lobes, i, cam, blur, tile_w, tile_h,
-                                     rects + 4 * (size_t)i, keys + i);
+    binned[i] = oracle_rule_rect_one(planes, pitch, n_lobes, i, cam, blur, b_lo, b_hi, tile_w,
+                                     tile_h, rects + 4 * (size_t)i, keys + i);
 }

@@ -548,3 +548,26 @@ def test_paper_constants_golden():
     assert abs(1.0 / (g["beta_c"] + 1) - g["beta_c_integral"]) < 1e-12
     assert abs((1 - math.exp(-4.5)) / 4.5 - g["gaussian_integral"]) < 1e-4
     assert abs(g["noise_b_prime"] - math.log(25.0)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# geometry decomposition (Sec. 4.3): render the primitives with b in a range
+# --------------------------------------------------------------------------
+
+def test_geometry_decomposition_equals_removing_primitives():
+    """Masking by b_lo <= b < b_hi renders exactly the scene without the other
+    primitives, and bins exactly the kept ones."""
+    sc = scenes.config_scene(1, n=600, seed=5)
+    cam = scenes.pinhole(*scenes.look_at((0.0, 0.0, -3.0)), 64, 48)
+    b = sc.planes[11, :sc.n]
+    thr = float(np.float32(b.mean()))
+    for lo, hi in ((-np.inf, thr), (thr, np.inf)):
+        keep = np.nonzero((b >= np.float32(lo)) & (b < np.float32(hi)))[0]
+        sub = np.ascontiguousarray(sc.planes[:, keep])
+        full = oracle.render_full(sc.planes, sc.n, sc.n_lobes, cam, b_lo=lo, b_hi=hi)
+        only = oracle.render_full(sub, len(keep), sc.n_lobes, cam)
+        assert np.array_equal(full[0], only[0]) and np.array_equal(full[1], only[1])
+        _, recs, _ = oracle.bin_pairs(sc.planes, sc.n, sc.n_lobes, [cam], b_lo=lo, b_hi=hi)
+        assert set(np.unique(recs)) <= set(keep)
+        _, recs_sub, _ = oracle.bin_pairs(sub, len(keep), sc.n_lobes, [cam])
+        assert len(recs) == len(recs_sub)
