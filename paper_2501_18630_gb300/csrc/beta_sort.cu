@@ -112,7 +112,9 @@ __global__ void k_sort_prep(uint32_t* ghist, uint32_t* counters, int64_t* d_coun
 }
 
 // Digit histograms of every pass at once; also clears the look-back table
-// of the sort (only the tiles that `count` needs).
+// of the sort (only the tiles that `count` needs).  Per warp and digit pass,
+// two rounds aggregate the lanes sharing a leader's digit, the rest add
+// themselves.
 __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __restrict__ keys,
                                                              int64_t count_host,
                                                              const int64_t* __restrict__ d_count,
@@ -135,13 +137,24 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
   const int lane = threadIdx.x & 31;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ((count + 31) & ~31ll);
        i += (int64_t)gridDim.x * blockDim.x) {
-    bool valid = i < count;
-    uint32_t k = valid ? keys[i] : 0u;
+    const bool valid = i < count;
+    const uint32_t k = valid ? keys[i] : 0u;
     for (int p = 0; p < npass; ++p) {
-      uint32_t d = valid ? ((k >> (8 * p)) & 255u) : 256u;
-      uint32_t peers = __match_any_sync(0xffffffffu, d);
-      int leader = __ffs(peers) - 1;
-      if (valid && lane == leader) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+      const uint32_t d = (k >> (8 * p)) & 255u;
+      // two rounds of "broadcast a leader's digit, count its peers": a digit
+      // shared by most of the warp costs one shared-memory atomic; the few
+      // lanes left add themselves (spread digits rarely collide)
+      uint32_t left = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+      for (int round = 0; round < 2; ++round) {
+        if (left == 0u) break;
+        const int leader = __ffs(left) - 1;
+        const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
+        const uint32_t peers = __ballot_sync(0xffffffffu, valid && d == dl) & left;
+        if (lane == leader) atomicAdd(&h[p][dl], (uint32_t)__popc(peers));
+        left &= ~peers;
+      }
+      if ((left >> lane) & 1u) atomicAdd(&h[p][d], 1u);
     }
   }
   __syncthreads();
@@ -152,7 +165,8 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
 }
 
 // One onesweep scatter pass over the 8-bit digit at `shift`.  Each CTA tile
-// of 4096 keys is ranked per warp (match_any), its digit counts are chained
+// of 4096 keys is ranked per warp (each lane ORs its bit into its digit's
+// peer mask in shared memory), its digit counts are chained
 // to the preceding tiles by decoupled look-back, the keys are reordered by
 // digit in shared memory, and then written out so that consecutive threads
 // write consecutive addresses of each digit's run.
@@ -164,6 +178,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   extern __shared__ uint32_t s_dyn[];
   uint32_t* s_key = s_dyn;                    // [kSortTile] keys in block-sorted order
   uint32_t* s_val = s_dyn + kSortTile;        // [kSortTile]
+  __shared__ uint32_t s_peer[kSortThreads / 32][256];
   __shared__ uint32_t s_whist[kSortThreads / 32][256];
   __shared__ uint32_t s_gbase[256];           // global start of each digit's run for this tile
   __shared__ uint32_t s_bexcl[256];           // start of each digit inside the tile
@@ -191,6 +206,8 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     __syncthreads();
   }
 
+#pragma unroll
+  for (int w = 0; w < kSortThreads / 32; ++w) s_peer[w][tid] = 0u;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
     __syncthreads();
@@ -213,13 +230,19 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     for (int it = 0; it < kSortItems; ++it) {
       const int64_t idx = seg + it * 32 + lane;
       const bool valid = idx < count;
-      const uint32_t d = valid ? ((key[it] >> shift) & 255u) : 256u;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      const uint32_t d = (key[it] >> shift) & 255u;
+      // peers with the same digit: each lane sets its bit in the digit's mask
+      if (valid) atomicOr(&s_peer[warp][d], 1u << lane);
+      __syncwarp();
+      const uint32_t peers = valid ? s_peer[warp][d] : 0u;
       const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
       const int leader = __ffs(peers) - 1;
-      const uint32_t base = valid ? s_whist[warp][d & 255u] : 0u;
+      const uint32_t base = valid ? s_whist[warp][d] : 0u;
       __syncwarp();
-      if (valid && lane == leader) s_whist[warp][d] = base + (uint32_t)__popc(peers);
+      if (valid && lane == leader) {
+        s_whist[warp][d] = base + (uint32_t)__popc(peers);
+        s_peer[warp][d] = 0u;
+      }
       __syncwarp();
       loc[it] = base + rank;
     }
@@ -470,6 +493,12 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
   uint32_t* gh_d = w.ghist;
   uint32_t* gh_t = w.ghist + kMaxPasses * 256;
 
+  static bool smem_set = false;   // 32 KB dynamic + ~20 KB static shared memory per CTA
+  if (!smem_set) {
+    if (cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kOnesweepSmem) != cudaSuccess)
+      return cudaGetLastError();
+    smem_set = true;
+  }
   k_sort_prep<<<1, 256, 0, s>>>(w.ghist, w.counters, d_count, d_status);
 
   // 1. stable sort of all records by depth key (4 passes of 8 bits)
