@@ -320,7 +320,7 @@ def main():
         bytes_alg = {"project": sc.n * n_planes * 4 + nrec * 76,
                      "bin_sort": nrec * 8 * 4 + K * 8 * 3,
                      "l1": rast.total_pixels * 3 * 4 * 3,
-                     "project_bwd": nrec * 40 * 2 + sc.n * n_planes * 8}.get(dom, 0)
+                     "project_bwd": nrec * 48 * 2 + sc.n * n_planes * 8}.get(dom, 0)
         achieved = bytes_alg / (stage_ms[dom] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None}

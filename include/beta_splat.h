@@ -119,7 +119,8 @@ int64_t beta_total_pixels(const beta_camera* cams /* host */, int32_t n_views);
  * look-back tables, scan sums). */
 size_t beta_binsort_workspace_bytes(int32_t pitch, int32_t n_views, int64_t pair_capacity,
                                     const beta_camera* cams /* host */, const beta_opts* opt);
-/* Workspace of beta_raster_bwd: per-record 2D gradients, 10 floats each. */
+/* Workspace of beta_raster_bwd: per-record 2D gradient sums, a 48-byte slot
+ * (10 floats used) per record. */
 size_t beta_grad2d_bytes(int32_t pitch, int32_t n_views);
 /* Workspace of beta_l1_loss (per-block partial sums). */
 size_t beta_l1_workspace_bytes(const beta_camera* cams /* host */, int32_t n_views);
@@ -221,7 +222,8 @@ int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color,
  * them into d mu', d Sigma', d o, d beta and d colour.
  *   sched     beta_schedule() output (persistent launch) or NULL
  *   dL_dcolor [3 x total_pixels] in (layout of color)
- *   grad2d    [beta_grad2d_bytes()] in/out: 10 floats per record, ACCUMULATED.
+ *   grad2d    [beta_grad2d_bytes()] in/out: one 48-byte slot per record (16-byte
+ *             aligned buffer), ACCUMULATED.
  *             It must hold zeros on entry: zero it once after allocation;
  *             beta_project_bwd clears every slot it consumes. */
 int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,

@@ -183,7 +183,7 @@ size_t beta_binsort_workspace_bytes(int32_t pitch, int32_t n_views, int64_t cap,
 
 size_t beta_grad2d_bytes(int32_t pitch, int32_t n_views) {
   if (pitch <= 0 || n_views <= 0) return 0;
-  return (size_t)pitch * n_views * kGrad2d * sizeof(float);
+  return (size_t)pitch * n_views * kGrad2dStride * sizeof(float);
 }
 
 size_t beta_l1_workspace_bytes(const beta_camera* cams, int32_t n_views) {

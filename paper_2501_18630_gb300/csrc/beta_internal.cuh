@@ -10,7 +10,8 @@
 namespace beta {
 
 constexpr int kThreads = 256;     // raster CTA: one 16x16 tile, one pixel per thread
-constexpr int kGrad2d = 10;       // d mu'(2), d Sigma'(3: a, b, c), d o, d beta, d colour(3)
+constexpr int kGrad2d = 10;       // 2D gradient sums per record (see beta_raster.cu)
+constexpr int kGrad2dStride = 12; // floats per record slot: 48 bytes, 16-byte aligned for vector atomics
 constexpr int kRecordF4 = 4;      // raster record: 4 x float4 = 64 bytes
 
 // Raster record of one (view, primitive), 64 bytes:

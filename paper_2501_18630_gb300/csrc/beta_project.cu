@@ -225,18 +225,18 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict_
     float go = 0.0f, gbeta = 0.0f;
     for (int v = 0; v < vt.n_views; ++v) {
       const ViewDev& V = vt.v[v];
-      float* g2 = grad2d + ((size_t)v * pitch + i) * kGrad2d;
-      float G[kGrad2d];
+      float4* g2 = reinterpret_cast<float4*>(grad2d + ((size_t)v * pitch + i) * kGrad2dStride);
+      const float4 ga4 = g2[0], gb4 = g2[1], gc4 = g2[2];
+      const float G[kGrad2d] = {ga4.x, ga4.y, ga4.z, ga4.w, gb4.x, gb4.y, gb4.z, gb4.w, gc4.x, gc4.y};
       bool any = false;
 #pragma unroll
-      for (int k = 0; k < kGrad2d; ++k) {
-        G[k] = g2[k];
-        any = any || (G[k] != 0.0f);
-      }
+      for (int k = 0; k < kGrad2d; ++k) any = any || (G[k] != 0.0f);
       if (!any) continue;
       // leave the accumulator zeroed for the next backward
-#pragma unroll
-      for (int k = 0; k < kGrad2d; ++k) g2[k] = 0.0f;
+      const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      g2[0] = z4;
+      g2[1] = z4;
+      g2[2] = z4;
       ViewGeo g;
       int rc[4];
       uint32_t kk;

@@ -36,6 +36,13 @@ namespace beta {
 
 namespace {
 
+// 16-byte vector atomic add (sm_90+), into a 16-byte aligned slot
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
+               : "memory");
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -383,13 +390,14 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
             G[6] = t * lb;
             T = Tk;
           }
-          float* gdst = grad2d + (size_t)s_ridx[s] * kGrad2d;
-          if (__popc(amask) <= 2) {
-            // few lanes: direct atomics beat the cross-lane reduction
+          float* gdst = grad2d + (size_t)s_ridx[s] * kGrad2dStride;
+          if (__popc(amask) <= 4) {
+            // few lanes: each adds its ten values with three vector atomics,
+            // cheaper than the cross-lane reduction
             if (act) {
-#pragma unroll
-              for (int q = 0; q < kGrad2d; ++q)
-                if (G[q] != 0.0f) atomicAdd(gdst + q, G[q]);
+              red_add_v4(gdst + 0, G[0], G[1], G[2], G[3]);
+              red_add_v4(gdst + 4, G[4], G[5], G[6], G[7]);
+              red_add_v4(gdst + 8, G[8], G[9], 0.0f, 0.0f);
             }
           } else {
             const float tot = warp_sum10(G, lane);
