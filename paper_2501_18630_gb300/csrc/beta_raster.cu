@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
             T = Tk;
           }
           float* gdst = grad2d + (size_t)s_ridx[s] * kGrad2dStride;
-          if (__popc(amask) <= 4) {
-            // few lanes: each adds its ten values with three vector atomics,
+          if (__popc(amask) <= 12) {
+            // up to 12 lanes: each adds its ten values with three vector atomics,
             // cheaper than the cross-lane reduction
             if (act) {
               red_add_v4(gdst + 0, G[0], G[1], G[2], G[3]);
