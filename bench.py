@@ -300,8 +300,8 @@ def main():
     # ---- roofline of the dominant kernel -----------------------------------
     hbm_peak, sm_max_mhz, peak_src = peaks()
     dom = max(stage_ms, key=stage_ms.get)
-    rec = rast.proj[: V * rast.pitch * 64].view(torch.float32).view(V, rast.pitch, 16)
-    keys = rast.proj[V * rast.pitch * 72: V * rast.pitch * 76].view(torch.int32).view(V, rast.pitch)
+    rec = rast.proj[: V * rast.pitch * 48].view(torch.float32).view(V, rast.pitch, 12)
+    keys = rast.proj[V * rast.pitch * 56: V * rast.pitch * 60].view(torch.int32).view(V, rast.pitch)
     binned = keys != -1
     area = math.pi / (rec[..., 4] * rec[..., 5]).clamp_min(1e-30)          # pi sqrt(det Sigma')
     evals = float(torch.where(binned, area.clamp_max(args.width * args.height), torch.zeros_like(area)).sum().item())
@@ -317,7 +317,7 @@ def main():
                 "algorithmic": f"{fl} flop x {evals:.4g} (pixel, Beta) evaluations inside the support (ellipse areas)"}
     else:
         nrec = V * sc.n
-        bytes_alg = {"project": sc.n * n_planes * 4 + nrec * 76,
+        bytes_alg = {"project": sc.n * n_planes * 4 + nrec * 60,
                      "bin_sort": nrec * 8 * 4 + K * 8 * 3,
                      "l1": rast.total_pixels * 3 * 4 * 3,
                      "project_bwd": nrec * 48 * 2 + sc.n * n_planes * 8}.get(dom, 0)
@@ -409,7 +409,7 @@ def main():
                                                               for c, v in tune_ms.items()}},
                    "n_betas": sc.n, "views_per_gpu": V, "resolution": f"{args.width}x{args.height}",
                    "pairs_per_step": K, "l2": f"inputs larger than L2: {sc.n * n_planes * 4 / 1e6:.0f} MB params + "
-                                               f"{V * sc.pitch * 76 / 1e6:.0f} MB records per step",
+                                               f"{V * sc.pitch * 60 / 1e6:.0f} MB records per step",
                    "parallelism": f"dp{world} over views"},
         "ms_per_view": ms_step / V,
         "stage_ms": stage_ms,

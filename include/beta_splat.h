@@ -108,8 +108,8 @@ int32_t beta_version(void);
 
 /* ---- sizes (host-only queries, no device work) ------------------------ */
 
-/* Bytes of the projection buffer `proj` for V views: 76 bytes per record
- * (64-byte raster record, 8-byte tile rectangle, 4-byte depth key). */
+/* Bytes of the projection buffer `proj` for V views: 60 bytes per record
+ * (48-byte raster record, 8-byte tile rectangle, 4-byte depth key). */
 size_t beta_proj_bytes(int32_t pitch, int32_t n_views);
 /* Total tiles of a batch of views (the length of tile_ranges is this + 1). */
 int64_t beta_total_tiles(const beta_camera* cams /* host */, int32_t n_views, const beta_opts* opt);

@@ -156,7 +156,7 @@ int32_t beta_version(void) { return kVersion; }
 
 size_t beta_proj_bytes(int32_t pitch, int32_t n_views) {
   if (pitch <= 0 || n_views <= 0) return 0;
-  return (size_t)pitch * n_views * 76;
+  return (size_t)pitch * n_views * (16 * kRecordF4 + 12);
 }
 
 int64_t beta_total_tiles(const beta_camera* cams, int32_t n_views, const beta_opts* opt) {

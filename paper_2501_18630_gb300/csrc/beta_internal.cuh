@@ -12,14 +12,14 @@ namespace beta {
 constexpr int kThreads = 256;     // raster CTA: one 16x16 tile, one pixel per thread
 constexpr int kGrad2d = 10;       // 2D gradient sums per record (see beta_raster.cu)
 constexpr int kGrad2dStride = 12; // floats per record slot: 48 bytes, 16-byte aligned for vector atomics
-constexpr int kRecordF4 = 4;      // raster record: 4 x float4 = 64 bytes
+constexpr int kRecordF4 = 3;      // raster record: 3 x float4 = 48 bytes
 
-// Raster record of one (view, primitive), 64 bytes:
+// Raster record of one (view, primitive), 48 bytes:
 //   f4[0] = (mx_int, my_int, off_x, off_y)  centre mu' = mx_int + 0.5 - off_x
 //   f4[1] = (p, q1, q2, beta)               whitening: u = p dx, v = q2 dx + q1 dy, r^2 = u^2 + v^2
 //   f4[2] = (log2 o, c_r, c_g, c_b)
-//   f4[3] = (ex, ey, 1/o, 0)                conservative half extents of the support box, 1/opacity
 // Pixel (x, y) has dx = (x - mx_int) + off_x, which is exact up to one rounding.
+// The support r^2 < 1 spans |dx| <= 1/p and |dy| <= sqrt(p^2 + q2^2) / (p q1).
 
 struct ViewDev {
   float R[9];

@@ -28,8 +28,8 @@ ProjBuffers proj_layout(void* proj, int32_t pitch, int32_t n_views) {
   char* p = (char*)proj;
   size_t nrec = (size_t)pitch * n_views;
   b.rec = (float4*)p;
-  b.rect = (uint2*)(p + nrec * 64);
-  b.key = (uint32_t*)(p + nrec * 72);
+  b.rect = (uint2*)(p + nrec * 16 * kRecordF4);
+  b.key = (uint32_t*)(p + nrec * (16 * kRecordF4 + 8));
   return b;
 }
 
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
     int rc[4];
     uint32_t kk = 0xffffffffu;
     bool bin = ok && rule_depth(pg, V, g, kk) && rule_view(pg, V, ro.blur_eps, ro.tile_w, ro.tile_h, g, rc);
-    float4 o0, o1, o2, o3;
+    float4 o0, o1, o2;
     if (bin) {
       // projected centre in double-float
       dd tx = cam_coord_dd(V, 0, pg.mu), ty = cam_coord_dd(V, 1, pg.mu), tz = cam_coord_dd(V, 2, pg.mu);
@@ -164,19 +164,15 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
         float q2 = -(b * pp) / sd;
         float col[3];
         sb_colour<M>(p, at, V, ro.color_mode, col);
-        const float INFL = 1.000244140625f, PAD = 0.015625f;
-        float ex = sqrtf(g.sxx) * INFL + PAD, ey = sqrtf(g.syy) * INFL + PAD;
         o0 = make_float4(ix, iy, 0.5f - fx, 0.5f - fy);
         o1 = make_float4(pp, q1, q2, at.beta);
         o2 = make_float4(at.log2o, col[0], col[1], col[2]);
-        o3 = make_float4(ex, ey, 1.0f + expf(-p[10]), 0.0f);   // 1 / o
       }
     }
     if (bin) {
-      rec[r * 4 + 0] = o0;
-      rec[r * 4 + 1] = o1;
-      rec[r * 4 + 2] = o2;
-      rec[r * 4 + 3] = o3;
+      rec[r * kRecordF4 + 0] = o0;
+      rec[r * kRecordF4 + 1] = o1;
+      rec[r * kRecordF4 + 2] = o2;
       rect[r] = make_uint2((uint32_t)rc[0] | ((uint32_t)rc[1] << 16), (uint32_t)rc[2] | ((uint32_t)rc[3] << 16));
       key[r] = kk;
     } else {

@@ -49,45 +49,58 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// r^2 at offset (dx, dy) from the centre, for the whitening (p, q1, q2)
-__device__ __forceinline__ float r2_at(float p, float q1, float q2, float dx, float dy) {
-  const float u = p * dx;
-  const float v = fmaf(q2, dx, q1 * dy);
-  return fmaf(u, u, v * v);
+// Does the support r^2 < 1 of a record reach a pixel centre of the 8x4 block
+// whose first pixel is (bxf, byf)?  Conservative by a 1% margin on r^2: the
+// test is the minimum of the convex r^2 over the block's rectangle of pixel
+// centres, in closed form and without divisions.  With A = p^2 + q2^2:
+//   support box:    |dx| <= 1/p,  |dy| <= sqrt(A) / (p q1);
+//   vertical edge:  r^2(x, y) = (p x)^2 + (q2 x + q1 y)^2, and q2 x + q1 y is
+//                   increasing in y, so its square is least at the end
+//                   nearest zero (or zero between the ends);
+//   horizontal edge y: the interior minimum over x is (p q1 y)^2 / A, taken
+//                   when d/dx = 2 (A x + q1 q2 y) changes sign on the edge
+//                   (else the minimum is a corner, covered by the vertical edges).
+__device__ __forceinline__ bool block_hit(float4 f0, float4 f1, float bxf, float byf) {
+  const float p = f1.x, q1 = f1.y, q2 = f1.z;
+  const float x0 = (bxf - f0.x) + f0.z, x1 = x0 + 7.0f;
+  const float y0 = (byf - f0.y) + f0.w, y1 = y0 + 3.0f;
+  const float m = 1.01f;
+  const float A = fmaf(p, p, q2 * q2), pq = p * q1;
+  const float xn = x1 < 0.0f ? x1 : (x0 > 0.0f ? x0 : 0.0f);   // block point nearest the centre
+  const float yn = y1 < 0.0f ? y1 : (y0 > 0.0f ? y0 : 0.0f);
+  const float ux = p * xn, uy = pq * yn;
+  if (ux * ux > m || uy * uy > m * A) return false;              // outside the support box
+  if (xn == 0.0f && yn == 0.0f) return true;                     // centre inside the block
+  float best = 3.0e38f;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float xc = e ? x1 : x0;
+    const float w0 = fmaf(q2, xc, q1 * y0), w1 = fmaf(q2, xc, q1 * y1);
+    const float wm = w0 > 0.0f ? w0 : (w1 < 0.0f ? w1 : 0.0f);
+    const float u = p * xc;
+    best = fminf(best, fmaf(u, u, wm * wm));
+    const float yc = e ? y1 : y0;
+    const float B = q1 * q2 * yc, uc = pq * yc;
+    if (fmaf(A, x0, B) < 0.0f && fmaf(A, x1, B) > 0.0f && uc * uc < m * A) best = 0.0f;
+  }
+  return best < m;
 }
 
-// Bit w of the result is set when the support ellipse of a record can cover a
-// pixel centre of warp w's 8x4 block.  Exact up to a 1% margin on r^2: the
-// minimum of the convex r^2 over the block's rectangle of pixel centres is at
-// the ellipse centre if it lies inside, else on an edge, where it is the
-// clamped 1D minimiser.
-template <int TW, int TH>
-__device__ __forceinline__ uint32_t warp_mask(float4 f0, float4 f1, float4 f3, float tx0f, float ty0f) {
-  constexpr int NW = TW * TH / 32, BXW = TW / 8;
-  // centre relative to the tile origin, in pixel-index coordinates
-  const float rx = (f0.x - tx0f) - f0.z;
-  const float ry = (f0.y - ty0f) - f0.w;
-  const float ex = f3.x, ey = f3.y;
-  const float p = f1.x, q1 = f1.y, q2 = f1.z;
-  const float kv = -q2 / q1;                          // dy minimising r^2 at fixed dx, per unit dx
-  const float kh = -(q1 * q2) / fmaf(p, p, q2 * q2);  // dx minimising r^2 at fixed dy, per unit dy
-  uint32_t m = 0;
+// Asynchronous 16-byte global -> shared copies (LDGSTS), so record staging
+// for the next batch overlaps compositing of the current one.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  const size_t ga = __cvta_generic_to_global(gmem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(ga) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Stage record r (48 bytes) into a shared slot.
+__device__ __forceinline__ void stage_record(float4* dst, const float4* __restrict__ rec, uint32_t r) {
+  const float4* src = rec + (size_t)r * kRecordF4;
 #pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    const float bx = 8.0f * (w % BXW), by = 4.0f * (w / BXW);
-    const float x0 = bx - rx, x1 = bx + 7.0f - rx, y0 = by - ry, y1 = by + 3.0f - ry;
-    if (x1 < -ex || x0 > ex || y1 < -ey || y0 > ey) continue;   // bounding box misses the block
-    bool hit = (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f);
-    if (!hit) {
-      float r = r2_at(p, q1, q2, x0, fminf(fmaxf(kv * x0, y0), y1));
-      r = fminf(r, r2_at(p, q1, q2, x1, fminf(fmaxf(kv * x1, y0), y1)));
-      r = fminf(r, r2_at(p, q1, q2, fminf(fmaxf(kh * y0, x0), x1), y0));
-      r = fminf(r, r2_at(p, q1, q2, fminf(fmaxf(kh * y1, x0), x1), y1));
-      hit = r < 1.01f;
-    }
-    if (hit) m |= 1u << w;
-  }
-  return m;
+  for (int q = 0; q < kRecordF4; ++q) cp_async16(dst + q, src + q);
 }
 
 // Tile assignment: CTA b renders tile b, or (persistent) tiles are taken from
@@ -116,7 +129,7 @@ __device__ __forceinline__ void leave(uint32_t* ctr) {
 }
 
 template <int TW, int TH, int S, bool PERSIST>
-__global__ void __launch_bounds__(TW * TH) k_raster_fwd(ViewTable vt, RenderOpts ro,
+__global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTable vt, RenderOpts ro,
                                                        const float4* __restrict__ rec,
                                                        const uint32_t* __restrict__ vals,
                                                        const uint32_t* __restrict__ ranges,
@@ -125,9 +138,8 @@ __global__ void __launch_bounds__(TW * TH) k_raster_fwd(ViewTable vt, RenderOpts
                                                        uint32_t* __restrict__ ncontrib,
                                                        const int32_t* __restrict__ status,
                                                        uint32_t* ctr, const uint32_t* __restrict__ order) {
-  constexpr int NT = TW * TH, BXW = TW / 8;
-  __shared__ float4 s_rec[S][3];
-  __shared__ uint32_t s_mask[S];
+  constexpr int NT = TW * TH, BXW = TW / 8, RPT = (S + NT - 1) / NT;
+  __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
   __shared__ int s_item;
   if (*status != 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -139,53 +151,63 @@ __global__ void __launch_bounds__(TW * TH) k_raster_fwd(ViewTable vt, RenderOpts
     const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
     const int lt = g - vt.v[v].tile_off;
     const int ty = lt / ntx, tx = lt - ty * ntx;
-    const int x = tx * TW + (warp % BXW) * 8 + (lane & 7);
-    const int y = ty * TH + (warp / BXW) * 4 + (lane >> 3);
+    const int bx = tx * TW + (warp % BXW) * 8, by = ty * TH + (warp / BXW) * 4;
+    const int x = bx + (lane & 7), y = by + (lane >> 3);
     const bool inside = x < W && y < H;
-    const float xf = (float)x, yf = (float)y;
-    const float tx0f = (float)(tx * TW), ty0f = (float)(ty * TH);
+    const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
     const uint32_t start = ranges[g], end = ranges[g + 1];
+
+    // batch 0 goes to buffer 0 now; the list entries of batch 1 are loaded
+    // ahead so that its copies can be issued without waiting on them
+    uint32_t rn[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int jj = tid + q * NT;
+      if (jj < S && start + jj < end) stage_record(s_rec[0][jj], rec, vals[start + jj]);
+      const uint32_t j1 = start + S + jj;
+      rn[q] = (jj < S && j1 < end) ? vals[j1] : 0u;
+    }
+    cp_async_commit();
 
     float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
     uint32_t last = 0;
     bool done = !inside;
     bool warp_done = __all_sync(0xffffffffu, done);
 
+    int buf = 0;
     for (uint32_t base = start; base < end; base += S) {
+      cp_async_wait_all();
       if (!__syncthreads_or(!done)) break;
-      for (int jj = tid; jj < S; jj += NT) {
-        const uint32_t j = base + jj;
-        if (j < end) {
-          const uint32_t r = vals[j];
-          const float4 f0 = rec[(size_t)r * 4 + 0];
-          const float4 f1 = rec[(size_t)r * 4 + 1];
-          const float4 f2 = rec[(size_t)r * 4 + 2];
-          const float4 f3 = rec[(size_t)r * 4 + 3];
-          s_rec[jj][0] = f0;
-          s_rec[jj][1] = f1;
-          s_rec[jj][2] = f2;
-          s_mask[jj] = warp_mask<TW, TH>(f0, f1, f3, tx0f, ty0f);
-        }
+      // copies of the next batch into the other buffer (free: every warp has
+      // passed the barrier after compositing from it), entries of the one after
+      const uint32_t nb = base + S;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int jj = tid + q * NT;
+        if (jj < S && nb + jj < end) stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
+        const uint32_t j2 = nb + S + jj;
+        rn[q] = (jj < S && j2 < end) ? vals[j2] : 0u;
       }
-      __syncthreads();
+      cp_async_commit();
       const int cnt = (int)min((uint32_t)S, end - base);
       for (int c = 0; c < cnt && !warp_done; c += 32) {
+        // lane k tests record c + k against this warp's block
         const int idx = c + lane;
-        const bool bit = idx < cnt && ((s_mask[idx] >> warp) & 1u);
+        const bool bit = idx < cnt && block_hit(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf);
         uint32_t bits = __ballot_sync(0xffffffffu, bit);
         while (bits) {
           const int k = __ffs(bits) - 1;
           bits &= bits - 1;
           const int s = c + k;
-          const float4 f0 = s_rec[s][0];
-          const float4 f1 = s_rec[s][1];
+          const float4 f0 = s_rec[buf][s][0];
+          const float4 f1 = s_rec[buf][s][1];
           const float dx = (xf - f0.x) + f0.z;
           const float dy = (yf - f0.y) + f0.w;
           const float u = f1.x * dx;
           const float vv = fmaf(f1.z, dx, f1.y * dy);
           const float r2 = fmaf(u, u, vv * vv);
           if (!done && r2 < 1.0f) {
-            const float4 f2 = s_rec[s][2];
+            const float4 f2 = s_rec[buf][s][2];
             const float lb = lg2_approx(1.0f - r2);
             float a = ex2_approx(fmaf(f1.w, lb, f2.x));
             a = fminf(a, amax);
@@ -200,7 +222,9 @@ __global__ void __launch_bounds__(TW * TH) k_raster_fwd(ViewTable vt, RenderOpts
         }
         warp_done = __all_sync(0xffffffffu, done);
       }
+      buf ^= 1;
     }
+    cp_async_wait_all();   // no copy may still land in a buffer the next tile fills
     if (inside) {
       const int64_t HW = (int64_t)W * H;
       const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
@@ -273,10 +297,9 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
                                                        float* __restrict__ grad2d,
                                                        const int32_t* __restrict__ status,
                                                        uint32_t* ctr, const uint32_t* __restrict__ order) {
-  constexpr int NT = TW * TH, NW = NT / 32, BXW = TW / 8;
-  __shared__ float4 s_rec[S][4];
-  __shared__ uint32_t s_mask[S];
-  __shared__ uint32_t s_ridx[S];
+  constexpr int NT = TW * TH, NW = NT / 32, BXW = TW / 8, RPT = (S + NT - 1) / NT;
+  __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
+  __shared__ uint32_t s_ridx[2][S];
   __shared__ uint32_t s_wmax[NW];
   __shared__ int s_item;
   if (*status != 0) return;
@@ -290,12 +313,11 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
     const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
     const int lt = g - vt.v[v].tile_off;
     const int ty = lt / ntx, tx = lt - ty * ntx;
-    const int x = tx * TW + (warp % BXW) * 8 + (lane & 7);
-    const int y = ty * TH + (warp / BXW) * 4 + (lane >> 3);
+    const int bx = tx * TW + (warp % BXW) * 8, by = ty * TH + (warp / BXW) * 4;
+    const int x = bx + (lane & 7), y = by + (lane >> 3);
     const bool inside = x < W && y < H;
-    const float xf = (float)x, yf = (float)y;
-    const float tx0f = (float)(tx * TW), ty0f = (float)(ty * TH);
-    const uint32_t start = ranges[g];
+    const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
+    const uint32_t* lst = vals + ranges[g];
 
     float T = 1.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, GS = 0.0f;
     uint32_t nl = 0;
@@ -313,40 +335,64 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
     const uint32_t wmax = __reduce_max_sync(0xffffffffu, nl);
     if (lane == 0) s_wmax[warp] = wmax;
     __syncthreads();
-    uint32_t bmax = 0;
+    int bmax = 0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) bmax = max(bmax, s_wmax[w]);
+    for (int w = 0; w < NW; ++w) bmax = max(bmax, (int)s_wmax[w]);
 
-    for (int top = (int)bmax; top > 0; top -= S) {
+    // Batches cover list positions [max(0, top - S), top) for top = bmax,
+    // bmax - S, ...  The first goes to buffer 0 now; the list entries of the
+    // second are loaded ahead so that its copies issue without waiting.
+    uint32_t rn[RPT];
+    {
+      const int lo0 = max(0, bmax - S), lo1 = max(0, bmax - 2 * S);
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int jj = tid + q * NT;
+        if (jj < bmax - lo0) {
+          const uint32_t r = lst[lo0 + jj];
+          s_ridx[0][jj] = r;
+          stage_record(s_rec[0][jj], rec, r);
+        }
+        rn[q] = (jj < bmax - S - lo1) ? lst[lo1 + jj] : 0u;
+      }
+      cp_async_commit();
+    }
+
+    int buf = 0;
+    for (int top = bmax; top > 0; top -= S) {
       const int lo = max(0, top - S);
       const int cnt = top - lo;
+      cp_async_wait_all();
       __syncthreads();
-      for (int jj = tid; jj < cnt; jj += NT) {
-        const uint32_t r = vals[start + lo + jj];
-        const float4 f0 = rec[(size_t)r * 4 + 0];
-        const float4 f1 = rec[(size_t)r * 4 + 1];
-        const float4 f2 = rec[(size_t)r * 4 + 2];
-        const float4 f3 = rec[(size_t)r * 4 + 3];
-        s_rec[jj][0] = f0;
-        s_rec[jj][1] = f1;
-        s_rec[jj][2] = f2;
-        s_rec[jj][3] = f3;
-        s_mask[jj] = warp_mask<TW, TH>(f0, f1, f3, tx0f, ty0f);
-        s_ridx[jj] = r;
+      {
+        // copies of the next batch into the other buffer, entries of the one after
+        const int t1 = top - S, lo1 = max(0, t1 - S);
+        const int t2 = top - 2 * S, lo2 = max(0, t2 - S);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          const int jj = tid + q * NT;
+          if (jj < t1 - lo1) {
+            s_ridx[buf ^ 1][jj] = rn[q];
+            stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
+          }
+          rn[q] = (jj < t2 - lo2) ? lst[lo2 + jj] : 0u;
+        }
+        cp_async_commit();
       }
-      __syncthreads();
       for (int c = ((cnt - 1) >> 5) << 5; c >= 0; c -= 32) {
         if ((uint32_t)(lo + c) >= wmax) continue;
+        // lane k tests record c + k against this warp's block
         const int idx = c + lane;
-        const bool bit = idx < cnt && ((s_mask[idx] >> warp) & 1u) && (uint32_t)(lo + idx) < wmax;
+        const bool bit = idx < cnt && (uint32_t)(lo + idx) < wmax &&
+                         block_hit(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf);
         uint32_t bits = __ballot_sync(0xffffffffu, bit);
         while (bits) {
           const int k = 31 - __clz(bits);
           bits &= ~(1u << k);
           const int s = c + k;
           const uint32_t pos = (uint32_t)(lo + s);
-          const float4 f0 = s_rec[s][0];
-          const float4 f1 = s_rec[s][1];
+          const float4 f0 = s_rec[buf][s][0];
+          const float4 f1 = s_rec[buf][s][1];
           const float dx = (xf - f0.x) + f0.z;
           const float dy = (yf - f0.y) + f0.w;
           const float u = f1.x * dx;
@@ -364,7 +410,7 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
 #pragma unroll
           for (int q = 0; q < kGrad2d; ++q) G[q] = 0.0f;
           if (act) {
-            const float4 f2 = s_rec[s][2];
+            const float4 f2 = s_rec[buf][s][2];
             const float beta = f1.w;
             const float base = 1.0f - r2;
             const float lb = lg2_approx(base);
@@ -390,7 +436,7 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
             G[6] = t * lb;
             T = Tk;
           }
-          float* gdst = grad2d + (size_t)s_ridx[s] * kGrad2dStride;
+          float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
           if (__popc(amask) <= 12) {
             // up to 12 lanes: each adds its ten values with three vector atomics,
             // cheaper than the cross-lane reduction
@@ -405,7 +451,9 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
           }
         }
       }
+      buf ^= 1;
     }
+    cp_async_wait_all();   // no copy may still land in a buffer the next tile fills
     __syncthreads();
   }
   leave<PERSIST>(ctr);

@@ -111,10 +111,34 @@ __global__ void k_sort_prep(uint32_t* ghist, uint32_t* counters, int64_t* d_coun
   }
 }
 
+// Adds one key per lane to the per-pass digit histograms.  Per pass, two
+// rounds of "broadcast a leader's digit, count its peers": a digit shared by
+// most of the warp costs one shared-memory atomic; the few lanes left add
+// themselves (spread digits rarely collide).  Warp-uniform call.
+__device__ __forceinline__ void hist_add(uint32_t k, bool valid, int npass, uint32_t (*h)[256], int lane) {
+  const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+  if (vmask == 0u) return;
+  for (int p = 0; p < npass; ++p) {
+    const uint32_t d = (k >> (8 * p)) & 255u;
+    uint32_t left = vmask;
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+      if (left == 0u) break;
+      const int leader = __ffs(left) - 1;
+      const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
+      const uint32_t peers = __ballot_sync(0xffffffffu, valid && d == dl) & left;
+      if (lane == leader) atomicAdd(&h[p][dl], (uint32_t)__popc(peers));
+      left &= ~peers;
+    }
+    if ((left >> lane) & 1u) atomicAdd(&h[p][d], 1u);
+  }
+}
+
 // Digit histograms of every pass at once; also clears the look-back table
-// of the sort (only the tiles that `count` needs).  Per warp and digit pass,
-// two rounds aggregate the lanes sharing a leader's digit, the rest add
-// themselves.
+// of the sort (only the tiles that `count` needs).  Keys are read as 16-byte
+// vectors, kHistVec of them per thread in flight.
+constexpr int kHistVec = 4;
+
 __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __restrict__ keys,
                                                              int64_t count_host,
                                                              const int64_t* __restrict__ d_count,
@@ -123,7 +147,7 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
                                                              uint32_t* __restrict__ look,
                                                              int64_t look_stride_tiles) {
   __shared__ uint32_t h[kMaxPasses][256];
-  int64_t count = d_count ? min(*d_count, cap) : count_host;
+  const int64_t count = d_count ? min(*d_count, cap) : count_host;
   for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
   // clear the look-back entries of the tiles this sort will use (per pass)
   const int64_t nblk = (count + kSortTile - 1) / kSortTile;
@@ -135,27 +159,29 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ((count + 31) & ~31ll);
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const bool valid = i < count;
-    const uint32_t k = valid ? keys[i] : 0u;
-    for (int p = 0; p < npass; ++p) {
-      const uint32_t d = (k >> (8 * p)) & 255u;
-      // two rounds of "broadcast a leader's digit, count its peers": a digit
-      // shared by most of the warp costs one shared-memory atomic; the few
-      // lanes left add themselves (spread digits rarely collide)
-      uint32_t left = __ballot_sync(0xffffffffu, valid);
+  const int64_t nvec = count >> 2;
+  const uint4* kv = reinterpret_cast<const uint4*>(keys);
+  constexpr int64_t kRound = (int64_t)kSortThreads * kHistVec;
+  for (int64_t g0 = (int64_t)blockIdx.x * kRound; g0 < nvec; g0 += (int64_t)gridDim.x * kRound) {
+    uint4 q[kHistVec];
 #pragma unroll
-      for (int round = 0; round < 2; ++round) {
-        if (left == 0u) break;
-        const int leader = __ffs(left) - 1;
-        const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
-        const uint32_t peers = __ballot_sync(0xffffffffu, valid && d == dl) & left;
-        if (lane == leader) atomicAdd(&h[p][dl], (uint32_t)__popc(peers));
-        left &= ~peers;
-      }
-      if ((left >> lane) & 1u) atomicAdd(&h[p][d], 1u);
+    for (int i = 0; i < kHistVec; ++i) {
+      const int64_t idx = g0 + i * kSortThreads + threadIdx.x;
+      q[i] = idx < nvec ? kv[idx] : make_uint4(0u, 0u, 0u, 0u);
     }
+#pragma unroll
+    for (int i = 0; i < kHistVec; ++i) {
+      const bool ok = g0 + i * kSortThreads + threadIdx.x < nvec;
+      hist_add(q[i].x, ok, npass, h, lane);
+      hist_add(q[i].y, ok, npass, h, lane);
+      hist_add(q[i].z, ok, npass, h, lane);
+      hist_add(q[i].w, ok, npass, h, lane);
+    }
+  }
+  // the last count mod 4 keys
+  if (blockIdx.x == 0 && threadIdx.x < (int)(count & 3)) {
+    const uint32_t k = keys[(nvec << 2) + threadIdx.x];
+    for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) {
@@ -166,11 +192,13 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
 
 // One onesweep scatter pass over the 8-bit digit at `shift`.  Each CTA tile
 // of 4096 keys is ranked per warp (each lane ORs its bit into its digit's
-// peer mask in shared memory), its digit counts are chained
-// to the preceding tiles by decoupled look-back, the keys are reordered by
-// digit in shared memory, and then written out so that consecutive threads
-// write consecutive addresses of each digit's run.
-__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+// peer mask in shared memory), its digit counts are chained to the preceding
+// tiles by decoupled look-back, keys and then values are reordered by digit
+// in shared memory, and both are written out so that consecutive threads
+// write consecutive addresses of each digit's run.  Values are loaded only
+// after the keys have been placed, so that keys and values are never live in
+// registers together (occupancy: 4 CTAs per SM).
+__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int write_keys,
     const uint32_t* __restrict__ ghist, uint32_t* look, uint32_t* tile_counter, int64_t count_host,
@@ -186,8 +214,9 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   __shared__ uint32_t s_wsum[kSortThreads / 32];
   __shared__ uint32_t s_tile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t count = d_count ? min(*d_count, cap) : count_host;
-  const int64_t nblk = (count + kSortTile - 1) / kSortTile;
+  // counts fit in 31 bits (the pair capacity is checked on the host)
+  const uint32_t count = (uint32_t)(d_count ? min(*d_count, cap) : count_host);
+  const uint32_t nblk = (count + kSortTile - 1) / kSortTile;
 
   // exclusive scan of the global digit histogram (once per CTA)
   {
@@ -211,25 +240,22 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
     __syncthreads();
-    const int64_t tile = s_tile;
+    const uint32_t tile = s_tile;
     if (tile >= nblk) break;
 #pragma unroll
     for (int w = 0; w < kSortThreads / 32; ++w) s_whist[w][tid] = 0;
     __syncthreads();
 
-    const int64_t seg = tile * kSortTile + (int64_t)warp * (32 * kSortItems);
-    uint32_t key[kSortItems], val[kSortItems], loc[kSortItems];
+    const uint32_t seg = tile * kSortTile + (uint32_t)warp * (32 * kSortItems) + lane;
+    uint32_t key[kSortItems], loc[kSortItems];
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      const int64_t idx = seg + it * 32 + lane;
-      const bool valid = idx < count;
-      key[it] = valid ? keys_in[idx] : 0xffffffffu;
-      val[it] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+      const uint32_t idx = seg + it * 32;
+      key[it] = idx < count ? keys_in[idx] : 0xffffffffu;
     }
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      const int64_t idx = seg + it * 32 + lane;
-      const bool valid = idx < count;
+      const bool valid = seg + it * 32 < count;
       const uint32_t d = (key[it] >> shift) & 255u;
       // peers with the same digit: each lane sets its bit in the digit's mask
       if (valid) atomicOr(&s_peer[warp][d], 1u << lane);
@@ -270,13 +296,13 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
       s_bexcl[tid] = wpre + x - total;
     }
     // decoupled look-back for digit `tid`
-    uint32_t* my = look + tile * 256 + tid;
+    uint32_t* my = look + (size_t)tile * 256 + tid;
     uint32_t excl = 0;
     if (tile == 0) {
       atomicExch(my, kFlagInc | total);
     } else {
       atomicExch(my, kFlagAgg | total);
-      int64_t j = tile - 1;
+      int64_t j = (int64_t)tile - 1;
       while (j >= 0) {
         volatile uint32_t* pj = look + j * 256 + tid;
         uint32_t v = *pj;
@@ -297,20 +323,24 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     }
     s_gbase[tid] = s_gexcl[tid] + excl;
     __syncthreads();
-    // reorder by digit inside the tile
+    // keys to their place inside the tile; loc becomes the tile position
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
-      const int64_t idx = seg + it * 32 + lane;
-      if (idx < count) {
+      if (seg + it * 32 < count) {
         const uint32_t d = (key[it] >> shift) & 255u;
-        const uint32_t pos = s_bexcl[d] + s_whist[warp][d] + loc[it];
-        s_key[pos] = key[it];
-        s_val[pos] = val[it];
+        loc[it] += s_bexcl[d] + s_whist[warp][d];
+        s_key[loc[it]] = key[it];
       }
+    }
+    // values follow the keys
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+      const uint32_t idx = seg + it * 32;
+      if (idx < count) s_val[loc[it]] = vals_in ? vals_in[idx] : idx;
     }
     __syncthreads();
     // coalesced write-out: element i of the tile goes to its digit's run
-    const int n_here = (int)min((int64_t)kSortTile, count - tile * kSortTile);
+    const int n_here = (int)min((uint32_t)kSortTile, count - tile * kSortTile);
 #pragma unroll 4
     for (int i = tid; i < n_here; i += kSortThreads) {
       const uint32_t k = s_key[i];
@@ -495,14 +525,15 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
 
   static bool smem_set = false;   // 32 KB dynamic + ~20 KB static shared memory per CTA
   if (!smem_set) {
-    if (cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kOnesweepSmem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kOnesweepSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
       return cudaGetLastError();
     smem_set = true;
   }
   k_sort_prep<<<1, 256, 0, s>>>(w.ghist, w.counters, d_count, d_status);
 
   // 1. stable sort of all records by depth key (4 passes of 8 bits)
-  int grid_h = (int)std::min<int64_t>(cdiv(n_items, kSortThreads), (int64_t)persist * 2);
+  int grid_h = (int)std::min<int64_t>(cdiv(n_items, 4 * kSortThreads * kHistVec), (int64_t)persist * 2);
   if (grid_h < 1) grid_h = 1;
   k_digit_hist<<<grid_h, kSortThreads, 0, s>>>(pb.key, n_items, nullptr, n_items, 4, gh_d, w.look_d,
                                                nblk_d);
@@ -537,7 +568,7 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
   // 3. stable sort of the pairs by global tile id
   const uint32_t* final_keys = w.pkey_a;
   if (np_t > 0) {
-    int grid_th = (int)std::min<int64_t>(cdiv(cap, kSortThreads), (int64_t)persist * 2);
+    int grid_th = (int)std::min<int64_t>(cdiv(cap, 4 * kSortThreads * kHistVec), (int64_t)persist * 2);
     if (grid_th < 1) grid_th = 1;
     k_digit_hist<<<grid_th, kSortThreads, 0, s>>>(w.pkey_a, 0, d_count, cap, np_t, gh_t, w.look_t,
                                                   nblk_t);

@@ -42,14 +42,14 @@ def rasterize(planes_np, n, n_lobes, cams, opts=None, cap=None, check=True):
 
 
 def proj_arrays(rast):
-    """(records (V,pitch,16) f32, rects (V,pitch,4) int, keys (V,pitch) u32) from the proj buffer."""
+    """(records (V,pitch,12) f32, rects (V,pitch,4) int, keys (V,pitch) u32) from the proj buffer."""
     V, pitch = rast.V, rast.pitch
     raw = rast.proj.cpu().numpy()
     nrec = V * pitch
-    rec = raw[:nrec * 64].view(np.float32).reshape(V, pitch, 16)
-    rr = raw[nrec * 64:nrec * 72].view(np.uint32).reshape(V, pitch, 2)
+    rec = raw[:nrec * 48].view(np.float32).reshape(V, pitch, 12)
+    rr = raw[nrec * 48:nrec * 56].view(np.uint32).reshape(V, pitch, 2)
     rects = np.stack([rr[..., 0] & 0xFFFF, rr[..., 0] >> 16, rr[..., 1] & 0xFFFF, rr[..., 1] >> 16], -1).astype(np.int64)
-    keys = raw[nrec * 72:nrec * 76].view(np.uint32).reshape(V, pitch)
+    keys = raw[nrec * 56:nrec * 60].view(np.uint32).reshape(V, pitch)
     return rec, rects, keys
 
 

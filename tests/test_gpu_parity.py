@@ -47,7 +47,6 @@ def test_project_records_match_oracle(cfg, n, views):
         assert np.abs(Q - Qo).max() / 1 < 1 and np.max(np.abs(Q - Qo) / scale) < 2e-4
         assert np.max(np.abs(r[:, 7] - pr["beta"][b]) / pr["beta"][b]) < 2e-6
         assert np.max(np.abs(np.exp2(r[:, 8]) - pr["o"][b]) / pr["o"][b]) < 2e-6
-        assert np.max(np.abs(r[:, 14] * pr["o"][b] - 1.0)) < 2e-6   # 1 / o
         assert np.abs(r[:, 9:12] - pr["color"][b]).max() < 2e-6
 
 
