@@ -45,13 +45,12 @@ struct SortWs {
   uint32_t* dkey_b;
   uint32_t* dval_a;
   uint32_t* dval_b;
-  unsigned long long* bsum;
-  unsigned long long* boff;
+  unsigned long long* look_e;   // [nb_scan] emit look-back (flag | inclusive or aggregate count)
   uint32_t* pkey_a;
   uint32_t* pkey_b;
   uint32_t* pval_ws;
   uint32_t* ghist;      // [2][kMaxPasses][256]: depth sort, tile sort
-  uint32_t* counters;   // [2][kMaxPasses] look-back tile counters
+  uint32_t* counters;   // [2][kMaxPasses] look-back tile counters, then the emit ticket
   uint32_t* look_d;     // [4][nblk_d][256]
   uint32_t* look_t;     // [npass_t][nblk_t][256]
   size_t bytes;
@@ -80,13 +79,12 @@ static SortWs carve(void* base, int64_t n_items, int64_t cap, int total_tiles) {
   w.dkey_b = (uint32_t*)take(n_items * 4);
   w.dval_a = (uint32_t*)take(n_items * 4);
   w.dval_b = (uint32_t*)take(n_items * 4);
-  w.bsum = (unsigned long long*)take(nb_scan * 8);
-  w.boff = (unsigned long long*)take(nb_scan * 8);
+  w.look_e = (unsigned long long*)take(nb_scan * 8);
   w.pkey_a = (uint32_t*)take(cap * 4);
   w.pkey_b = (uint32_t*)take(cap * 4);
   w.pval_ws = (uint32_t*)take(cap * 4);
   w.ghist = (uint32_t*)take(2 * kMaxPasses * 256 * 4);
-  w.counters = (uint32_t*)take(2 * kMaxPasses * 4);
+  w.counters = (uint32_t*)take((2 * kMaxPasses + 1) * 4);
   w.look_d = (uint32_t*)take((size_t)4 * nblk_d * 256 * 4);
   w.look_t = (uint32_t*)take((size_t)(np_t > 0 ? np_t : 1) * nblk_t * 256 * 4);
   w.bytes = off;
@@ -101,10 +99,12 @@ size_t binsort_ws_bytes(int64_t n_items, int64_t cap, int total_tiles) {
 // kernels
 // ---------------------------------------------------------------------------
 
-__global__ void k_sort_prep(uint32_t* ghist, uint32_t* counters, int64_t* d_count, int32_t* status) {
+__global__ void k_sort_prep(uint32_t* ghist, uint32_t* counters, unsigned long long* look_e,
+                            int64_t nb_scan, int64_t* d_count, int32_t* status) {
   int t = threadIdx.x;
   for (int i = t; i < 2 * kMaxPasses * 256; i += blockDim.x) ghist[i] = 0;
-  if (t < 2 * kMaxPasses) counters[t] = 0;
+  for (int64_t i = t; i < nb_scan; i += blockDim.x) look_e[i] = 0ull;
+  if (t < 2 * kMaxPasses + 1) counters[t] = 0;
   if (t == 0) {
     *d_count = 0;
     *status = 0;
@@ -136,7 +136,9 @@ __device__ __forceinline__ void hist_add(uint32_t k, bool valid, int npass, uint
 
 // Digit histograms of every pass at once; also clears the look-back table
 // of the sort (only the tiles that `count` needs).  Keys are read as 16-byte
-// vectors, kHistVec of them per thread in flight.
+// vectors, kHistVec of them per thread in flight; each warp counts into its
+// own shared-memory histograms (no contention between warps), which are
+// summed at the end.
 constexpr int kHistVec = 4;
 
 __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __restrict__ keys,
@@ -146,9 +148,9 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
                                                              uint32_t* __restrict__ ghist,
                                                              uint32_t* __restrict__ look,
                                                              int64_t look_stride_tiles) {
-  __shared__ uint32_t h[kMaxPasses][256];
+  __shared__ uint32_t h[kSortThreads / 32][kMaxPasses][256];
   const int64_t count = d_count ? min(*d_count, cap) : count_host;
-  for (int i = threadIdx.x; i < kMaxPasses * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < (kSortThreads / 32) * kMaxPasses * 256; i += blockDim.x) (&h[0][0][0])[i] = 0;
   // clear the look-back entries of the tiles this sort will use (per pass)
   const int64_t nblk = (count + kSortTile - 1) / kSortTile;
   const int64_t used = nblk * 256;
@@ -158,7 +160,8 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < used; i += gstride) lp[i] = 0;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t (*hw)[256] = h[warp];
   const int64_t nvec = count >> 2;
   const uint4* kv = reinterpret_cast<const uint4*>(keys);
   constexpr int64_t kRound = (int64_t)kSortThreads * kHistVec;
@@ -172,20 +175,22 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
 #pragma unroll
     for (int i = 0; i < kHistVec; ++i) {
       const bool ok = g0 + i * kSortThreads + threadIdx.x < nvec;
-      hist_add(q[i].x, ok, npass, h, lane);
-      hist_add(q[i].y, ok, npass, h, lane);
-      hist_add(q[i].z, ok, npass, h, lane);
-      hist_add(q[i].w, ok, npass, h, lane);
+      hist_add(q[i].x, ok, npass, hw, lane);
+      hist_add(q[i].y, ok, npass, hw, lane);
+      hist_add(q[i].z, ok, npass, hw, lane);
+      hist_add(q[i].w, ok, npass, hw, lane);
     }
   }
   // the last count mod 4 keys
   if (blockIdx.x == 0 && threadIdx.x < (int)(count & 3)) {
     const uint32_t k = keys[(nvec << 2) + threadIdx.x];
-    for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
+    for (int p = 0; p < npass; ++p) atomicAdd(&hw[p][(k >> (8 * p)) & 255u], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) {
-    uint32_t c = (&h[0][0])[i];
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < kSortThreads / 32; ++w) c += (&h[w][0][0])[i];
     if (c) atomicAdd(&ghist[i], c);
   }
 }
@@ -383,88 +388,94 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
   return pre + inc - x;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_count_sums(const uint32_t* __restrict__ order,
-                                                             const uint2* __restrict__ rects,
-                                                             int64_t n_items,
-                                                             unsigned long long* __restrict__ bsum) {
-  __shared__ unsigned long long s_w[kSortThreads / 32];
-  int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
-  unsigned long long s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    int64_t j = base + k;
-    if (j < n_items) s += rect_count(rects[order[j]]);
-  }
-  unsigned long long total;
-  block_excl_scan(s, s_w, total);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
-}
+constexpr unsigned long long kEAgg = 1ull << 62, kEInc = 2ull << 62, kECount = (1ull << 62) - 1;
 
-__global__ void __launch_bounds__(1024) k_scan_sums(const unsigned long long* __restrict__ bsum,
-                                                    int64_t nb, unsigned long long* __restrict__ boff,
-                                                    int64_t* d_count, int64_t cap, int32_t* status) {
-  __shared__ unsigned long long s_w[32];
-  __shared__ unsigned long long s_carry;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_carry = 0;
-  __syncthreads();
-  for (int64_t c0 = 0; c0 < nb; c0 += 1024) {
-    int64_t i = c0 + threadIdx.x;
-    unsigned long long x = i < nb ? bsum[i] : 0ull;
-    unsigned long long inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_w[warp] = inc;
-    __syncthreads();
-    unsigned long long pre = 0, tot = 0;
-    for (int w = 0; w < 32; ++w) {
-      if (w < warp) pre += s_w[w];
-      tot += s_w[w];
-    }
-    unsigned long long carry = s_carry;
-    if (i < nb) boff[i] = carry + pre + inc - x;
-    __syncthreads();
-    if (threadIdx.x == 0) s_carry = carry + tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    unsigned long long K = s_carry;
-    *d_count = (int64_t)K;
-    if ((int64_t)K > cap) set_status(status, BETA_ERR_CAPACITY);
-  }
-}
-
+// Pair counts of the records in depth order, their exclusive scan and the
+// emission of (global tile, record) pairs, in one pass: each CTA takes the
+// next block of kScanTile records from a ticket, reduces its counts, chains
+// its offset to the preceding blocks by decoupled look-back (warp 0 inspects
+// 32 predecessors at a time; bounded waits) and writes its pairs.  The last
+// block publishes the pair count K and flags a capacity overflow.
 __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restrict__ order,
                                                        const uint2* __restrict__ rects,
                                                        int64_t n_items, int pitch, ViewTable vt,
-                                                       const unsigned long long* __restrict__ boff,
+                                                       unsigned long long* look, uint32_t* ticket,
                                                        uint32_t* __restrict__ pkey,
-                                                       uint32_t* __restrict__ pval, int64_t cap) {
+                                                       uint32_t* __restrict__ pval, int64_t cap,
+                                                       int64_t* d_count, int32_t* status) {
   __shared__ unsigned long long s_w[kSortThreads / 32];
-  int64_t base = (int64_t)blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+  __shared__ unsigned long long s_base;
+  __shared__ uint32_t s_blk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int64_t blk = s_blk;
+  const int64_t nb = (n_items + kScanTile - 1) / kScanTile;
+  if (blk >= nb) return;
+  const int64_t base = blk * kScanTile + threadIdx.x * kScanItems;
   uint32_t rec[kScanItems];
   uint2 rc[kScanItems];
-  unsigned long long s = 0;
+  unsigned long long cnt = 0;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    int64_t j = base + k;
+    const int64_t j = base + k;
     rec[k] = j < n_items ? order[j] : 0u;
     rc[k] = j < n_items ? rects[rec[k]] : make_uint2(1u, 1u);
-    s += rect_count(rc[k]);
+    cnt += rect_count(rc[k]);
   }
   unsigned long long total;
-  unsigned long long off = boff[blockIdx.x] + block_excl_scan(s, s_w, total);
+  const unsigned long long excl = block_excl_scan(cnt, s_w, total);
+  if (warp == 0) {
+    unsigned long long prefix = 0;
+    if (blk == 0) {
+      if (lane == 0) atomicExch(&look[0], kEInc | total);
+    } else {
+      if (lane == 0) atomicExch(&look[blk], kEAgg | total);
+      for (int64_t j0 = blk - 1;; j0 -= 32) {
+        const int64_t j = j0 - lane;            // lane 0: the nearest predecessor
+        unsigned long long v = kEInc;           // before block 0: an inclusive zero
+        if (j >= 0) {
+          volatile unsigned long long* pj = look + j;
+          v = *pj;
+          int spins = 0;
+          while ((v & ~kECount) == 0ull) {
+            if (++spins > kSpinLimit) {
+              set_status(status, BETA_ERR_TIMEOUT);
+              v = kEInc;
+              break;
+            }
+            __nanosleep(64);
+            v = *pj;
+          }
+        }
+        const uint32_t inc = __ballot_sync(0xffffffffu, (v & ~kECount) == kEInc);
+        const int first = inc ? __ffs(inc) - 1 : 31;   // sum up to the nearest inclusive entry
+        unsigned long long mine = lane <= first ? (v & kECount) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+        prefix += mine;
+        if (inc) break;
+      }
+      if (lane == 0) atomicExch(&look[blk], kEInc | (prefix + total));
+    }
+    if (lane == 0) {
+      s_base = prefix;
+      if (blk == nb - 1) {
+        *d_count = (int64_t)(prefix + total);
+        if ((int64_t)(prefix + total) > cap) set_status(status, BETA_ERR_CAPACITY);
+      }
+    }
+  }
+  __syncthreads();
+  unsigned long long off = s_base + excl;
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
-    uint32_t c = rect_count(rc[k]);
+    const uint32_t c = rect_count(rc[k]);
     if (c == 0) continue;
-    int v = (int)(rec[k] / (uint32_t)pitch);
-    int ntx = vt.v[v].ntx, toff = vt.v[v].tile_off;
-    int tx0 = (int)(rc[k].x & 0xffffu), tx1 = (int)(rc[k].x >> 16);
-    int ty0 = (int)(rc[k].y & 0xffffu), ty1 = (int)(rc[k].y >> 16);
+    const int v = (int)(rec[k] / (uint32_t)pitch);
+    const int ntx = vt.v[v].ntx, toff = vt.v[v].tile_off;
+    const int tx0 = (int)(rc[k].x & 0xffffu), tx1 = (int)(rc[k].x >> 16);
+    const int ty0 = (int)(rc[k].y & 0xffffu), ty1 = (int)(rc[k].y >> 16);
     for (int ty = ty0; ty <= ty1; ++ty)
       for (int tx = tx0; tx <= tx1; ++tx) {
         if ((int64_t)off < cap) {
@@ -530,7 +541,7 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
       return cudaGetLastError();
     smem_set = true;
   }
-  k_sort_prep<<<1, 256, 0, s>>>(w.ghist, w.counters, d_count, d_status);
+  k_sort_prep<<<1, 256, 0, s>>>(w.ghist, w.counters, w.look_e, cdiv(n_items, kScanTile), d_count, d_status);
 
   // 1. stable sort of all records by depth key (4 passes of 8 bits)
   int grid_h = (int)std::min<int64_t>(cdiv(n_items, 4 * kSortThreads * kHistVec), (int64_t)persist * 2);
@@ -558,12 +569,10 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
   // final tile-sorted values must land in pair_vals: choose the emit buffer by pass parity
   uint32_t* pval_emit = (np_t % 2 == 0) ? pair_vals : w.pval_ws;
   uint32_t* pval_other = (np_t % 2 == 0) ? w.pval_ws : pair_vals;
-  if (nb_scan > 0) {
-    k_count_sums<<<(unsigned)nb_scan, kSortThreads, 0, s>>>(order, pb.rect, n_items, w.bsum);
-    k_scan_sums<<<1, 1024, 0, s>>>(w.bsum, nb_scan, w.boff, d_count, cap, d_status);
-    k_emit<<<(unsigned)nb_scan, kSortThreads, 0, s>>>(order, pb.rect, n_items, pitch, vt, w.boff,
-                                                       w.pkey_a, pval_emit, cap);
-  }
+  if (nb_scan > 0)
+    k_emit<<<(unsigned)nb_scan, kSortThreads, 0, s>>>(order, pb.rect, n_items, pitch, vt, w.look_e,
+                                                       w.counters + 2 * kMaxPasses, w.pkey_a, pval_emit,
+                                                       cap, d_count, d_status);
 
   // 3. stable sort of the pairs by global tile id
   const uint32_t* final_keys = w.pkey_a;
