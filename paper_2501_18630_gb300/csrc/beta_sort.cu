@@ -49,17 +49,23 @@ struct SortWs {
   uint32_t* pkey_a;
   uint32_t* pkey_b;
   uint32_t* pval_ws;
-  uint32_t* ghist;      // [2][kMaxPasses][256]: depth sort, tile sort
+  uint32_t* ghist;      // [2][kMaxPasses][512]: depth sort, tile sort
   uint32_t* counters;   // [2][kMaxPasses] look-back tile counters, then the emit ticket
   uint32_t* look_d;     // [4][nblk_d][256]
-  uint32_t* look_t;     // [npass_t][nblk_t][256]
+  uint32_t* look_t;     // [npass_t][nblk_t][radix_t]
   size_t bytes;
 };
 
-static int tile_passes(int total_tiles) {
-  int bits = 0;
-  while ((1ll << bits) < (int64_t)total_tiles) ++bits;
-  return (bits + 7) / 8;
+// Digit plan of the tile-id sort: 8-bit passes, except that 17- or 18-bit
+// tile ids take two 9-bit passes instead of three 8-bit ones.
+struct TilePlan {
+  int passes, bits;
+};
+static TilePlan tile_plan(int total_tiles) {
+  int b = 0;
+  while ((1ll << b) < (int64_t)total_tiles) ++b;
+  if (b == 17 || b == 18) return {2, 9};
+  return {(b + 7) / 8, 8};
 }
 
 static SortWs carve(void* base, int64_t n_items, int64_t cap, int total_tiles) {
@@ -74,7 +80,7 @@ static SortWs carve(void* base, int64_t n_items, int64_t cap, int total_tiles) {
   int64_t nblk_d = cdiv(n_items, kSortTile);
   int64_t nblk_t = cdiv(cap > 0 ? cap : 1, kSortTile);
   int64_t nb_scan = cdiv(n_items, kScanTile);
-  int np_t = tile_passes(total_tiles);
+  const TilePlan tp = tile_plan(total_tiles);
   w.dkey_a = (uint32_t*)take(n_items * 4);
   w.dkey_b = (uint32_t*)take(n_items * 4);
   w.dval_a = (uint32_t*)take(n_items * 4);
@@ -83,10 +89,10 @@ static SortWs carve(void* base, int64_t n_items, int64_t cap, int total_tiles) {
   w.pkey_a = (uint32_t*)take(cap * 4);
   w.pkey_b = (uint32_t*)take(cap * 4);
   w.pval_ws = (uint32_t*)take(cap * 4);
-  w.ghist = (uint32_t*)take(2 * kMaxPasses * 256 * 4);
+  w.ghist = (uint32_t*)take(2 * kMaxPasses * 512 * 4);
   w.counters = (uint32_t*)take((2 * kMaxPasses + 1) * 4);
   w.look_d = (uint32_t*)take((size_t)4 * nblk_d * 256 * 4);
-  w.look_t = (uint32_t*)take((size_t)(np_t > 0 ? np_t : 1) * nblk_t * 256 * 4);
+  w.look_t = (uint32_t*)take((size_t)(tp.passes > 0 ? tp.passes : 1) * nblk_t * (1 << tp.bits) * 4);
   w.bytes = off;
   return w;
 }
@@ -102,7 +108,7 @@ size_t binsort_ws_bytes(int64_t n_items, int64_t cap, int total_tiles) {
 __global__ void k_sort_prep(uint32_t* ghist, uint32_t* counters, unsigned long long* look_e,
                             int64_t nb_scan, int64_t* d_count, int32_t* status) {
   int t = threadIdx.x;
-  for (int i = t; i < 2 * kMaxPasses * 256; i += blockDim.x) ghist[i] = 0;
+  for (int i = t; i < 2 * kMaxPasses * 512; i += blockDim.x) ghist[i] = 0;
   for (int64_t i = t; i < nb_scan; i += blockDim.x) look_e[i] = 0ull;
   if (t < 2 * kMaxPasses + 1) counters[t] = 0;
   if (t == 0) {
@@ -111,15 +117,18 @@ __global__ void k_sort_prep(uint32_t* ghist, uint32_t* counters, unsigned long l
   }
 }
 
-// Adds one key per lane to the per-pass digit histograms.  Per pass, two
-// rounds of "broadcast a leader's digit, count its peers": a digit shared by
-// most of the warp costs one shared-memory atomic; the few lanes left add
-// themselves (spread digits rarely collide).  Warp-uniform call.
-__device__ __forceinline__ void hist_add(uint32_t k, bool valid, int npass, uint32_t (*h)[256], int lane) {
+// Adds one key per lane to the per-pass digit histograms (BITS-bit digits).
+// Per pass, two rounds of "broadcast a leader's digit, count its peers": a
+// digit shared by most of the warp costs one shared-memory atomic; the few
+// lanes left add themselves (spread digits rarely collide).  Warp-uniform call.
+template <int BITS>
+__device__ __forceinline__ void hist_add(uint32_t k, bool valid, int npass, uint32_t (*h)[1 << BITS],
+                                         int lane) {
+  constexpr uint32_t kMask = (1u << BITS) - 1u;
   const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
   if (vmask == 0u) return;
   for (int p = 0; p < npass; ++p) {
-    const uint32_t d = (k >> (8 * p)) & 255u;
+    const uint32_t d = (k >> (BITS * p)) & kMask;
     uint32_t left = vmask;
 #pragma unroll
     for (int round = 0; round < 2; ++round) {
@@ -134,13 +143,14 @@ __device__ __forceinline__ void hist_add(uint32_t k, bool valid, int npass, uint
   }
 }
 
-// Digit histograms of every pass at once; also clears the look-back table
-// of the sort (only the tiles that `count` needs).  Keys are read as 16-byte
-// vectors, kHistVec of them per thread in flight; each warp counts into its
-// own shared-memory histograms (no contention between warps), which are
-// summed at the end.
+// Digit histograms of every pass at once (at most NPMAX passes of BITS
+// bits); also clears the look-back table of the sort (only the tiles that
+// `count` needs).  Keys are read as 16-byte vectors, kHistVec of them per
+// thread in flight; each warp counts into its own shared-memory histograms
+// (no contention between warps), which are summed at the end.
 constexpr int kHistVec = 4;
 
+template <int BITS, int NPMAX>
 __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __restrict__ keys,
                                                              int64_t count_host,
                                                              const int64_t* __restrict__ d_count,
@@ -148,20 +158,21 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
                                                              uint32_t* __restrict__ ghist,
                                                              uint32_t* __restrict__ look,
                                                              int64_t look_stride_tiles) {
-  __shared__ uint32_t h[kSortThreads / 32][kMaxPasses][256];
+  constexpr int R = 1 << BITS;
+  __shared__ uint32_t h[kSortThreads / 32][NPMAX][R];
   const int64_t count = d_count ? min(*d_count, cap) : count_host;
-  for (int i = threadIdx.x; i < (kSortThreads / 32) * kMaxPasses * 256; i += blockDim.x) (&h[0][0][0])[i] = 0;
+  for (int i = threadIdx.x; i < (kSortThreads / 32) * NPMAX * R; i += blockDim.x) (&h[0][0][0])[i] = 0;
   // clear the look-back entries of the tiles this sort will use (per pass)
   const int64_t nblk = (count + kSortTile - 1) / kSortTile;
-  const int64_t used = nblk * 256;
+  const int64_t used = nblk * R;
   const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
   for (int p = 0; p < npass; ++p) {
-    uint32_t* lp = look + (int64_t)p * look_stride_tiles * 256;
+    uint32_t* lp = look + (int64_t)p * look_stride_tiles * R;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < used; i += gstride) lp[i] = 0;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t (*hw)[256] = h[warp];
+  uint32_t (*hw)[R] = h[warp];
   const int64_t nvec = count >> 2;
   const uint4* kv = reinterpret_cast<const uint4*>(keys);
   constexpr int64_t kRound = (int64_t)kSortThreads * kHistVec;
@@ -175,19 +186,19 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
 #pragma unroll
     for (int i = 0; i < kHistVec; ++i) {
       const bool ok = g0 + i * kSortThreads + threadIdx.x < nvec;
-      hist_add(q[i].x, ok, npass, hw, lane);
-      hist_add(q[i].y, ok, npass, hw, lane);
-      hist_add(q[i].z, ok, npass, hw, lane);
-      hist_add(q[i].w, ok, npass, hw, lane);
+      hist_add<BITS>(q[i].x, ok, npass, hw, lane);
+      hist_add<BITS>(q[i].y, ok, npass, hw, lane);
+      hist_add<BITS>(q[i].z, ok, npass, hw, lane);
+      hist_add<BITS>(q[i].w, ok, npass, hw, lane);
     }
   }
   // the last count mod 4 keys
   if (blockIdx.x == 0 && threadIdx.x < (int)(count & 3)) {
     const uint32_t k = keys[(nvec << 2) + threadIdx.x];
-    for (int p = 0; p < npass; ++p) atomicAdd(&hw[p][(k >> (8 * p)) & 255u], 1u);
+    for (int p = 0; p < npass; ++p) atomicAdd(&hw[p][(k >> (BITS * p)) & (uint32_t)(R - 1)], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < npass * 256; i += blockDim.x) {
+  for (int i = threadIdx.x; i < npass * R; i += blockDim.x) {
     uint32_t c = 0;
 #pragma unroll
     for (int w = 0; w < kSortThreads / 32; ++w) c += (&h[w][0][0])[i];
@@ -195,27 +206,63 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const uint32_t* __r
   }
 }
 
-// One onesweep scatter pass over the 8-bit digit at `shift`.  Each CTA tile
-// of 4096 keys is ranked per warp (each lane ORs its bit into its digit's
-// peer mask in shared memory), its digit counts are chained to the preceding
-// tiles by decoupled look-back, keys and then values are reordered by digit
-// in shared memory, and both are written out so that consecutive threads
-// write consecutive addresses of each digit's run.  Values are loaded only
-// after the keys have been placed, so that keys and values are never live in
-// registers together (occupancy: 4 CTAs per SM).
-__global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
+// Block-wide exclusive scan of DPT consecutive values per thread (thread t
+// holds entries t*DPT .. t*DPT+DPT-1); returns the total.
+template <int DPT>
+__device__ __forceinline__ uint32_t block_scan_digits(const uint32_t (&c)[DPT], uint32_t (&excl)[DPT],
+                                                      uint32_t* s_wsum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t local = 0;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) local += c[q];
+  uint32_t x = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_wsum[warp] = x;
+  __syncthreads();
+  uint32_t wpre = 0, tot = 0;
+  for (int w = 0; w < kSortThreads / 32; ++w) {
+    if (w < warp) wpre += s_wsum[w];
+    tot += s_wsum[w];
+  }
+  uint32_t run = wpre + x - local;
+#pragma unroll
+  for (int q = 0; q < DPT; ++q) {
+    excl[q] = run;
+    run += c[q];
+  }
+  __syncthreads();
+  return tot;
+}
+
+// One onesweep scatter pass over the BITS-bit digit at `shift`.  Each CTA
+// tile of 4096 keys is ranked per warp (each lane ORs its bit into its
+// digit's peer mask in shared memory), its digit counts are chained to the
+// preceding tiles by decoupled look-back, keys and then values are reordered
+// by digit in shared memory, and both are written out so that consecutive
+// threads write consecutive addresses of each digit's run.  Values are
+// loaded only after the keys have been placed, so that keys and values are
+// never live in registers together.  Thread t owns digits t*DPT .. +DPT-1 in
+// the per-digit steps (scans, look-back).
+template <int BITS>
+__global__ void __launch_bounds__(kSortThreads, BITS == 8 ? 4 : 3) k_onesweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int write_keys,
     const uint32_t* __restrict__ ghist, uint32_t* look, uint32_t* tile_counter, int64_t count_host,
     const int64_t* __restrict__ d_count, int64_t cap, int shift, int32_t* status) {
+  constexpr int R = 1 << BITS, DPT = R / kSortThreads;
+  constexpr uint32_t kMask = (uint32_t)R - 1u;
   extern __shared__ uint32_t s_dyn[];
   uint32_t* s_key = s_dyn;                    // [kSortTile] keys in block-sorted order
   uint32_t* s_val = s_dyn + kSortTile;        // [kSortTile]
-  __shared__ uint32_t s_peer[kSortThreads / 32][256];
-  __shared__ uint32_t s_whist[kSortThreads / 32][256];
-  __shared__ uint32_t s_gbase[256];           // global start of each digit's run for this tile
-  __shared__ uint32_t s_bexcl[256];           // start of each digit inside the tile
-  __shared__ uint32_t s_gexcl[256];
+  __shared__ uint32_t s_peer[kSortThreads / 32][R];
+  __shared__ uint32_t s_whist[kSortThreads / 32][R];
+  __shared__ uint32_t s_gbase[R];             // global start of each digit's run for this tile
+  __shared__ uint32_t s_bexcl[R];             // start of each digit inside the tile
+  __shared__ uint32_t s_gexcl[R];
   __shared__ uint32_t s_wsum[kSortThreads / 32];
   __shared__ uint32_t s_tile;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -225,30 +272,21 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
 
   // exclusive scan of the global digit histogram (once per CTA)
   {
-    const uint32_t c = ghist[tid];
-    uint32_t x = c;
+    uint32_t c[DPT], e[DPT];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_wsum[warp] = x;
-    __syncthreads();
-    uint32_t wpre = 0;
-    for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
-    s_gexcl[tid] = wpre + x - c;
-    __syncthreads();
+    for (int q = 0; q < DPT; ++q) c[q] = ghist[tid * DPT + q];
+    block_scan_digits<DPT>(c, e, s_wsum);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) s_gexcl[tid * DPT + q] = e[q];
   }
 
-#pragma unroll
-  for (int w = 0; w < kSortThreads / 32; ++w) s_peer[w][tid] = 0u;
+  for (int i = tid; i < (kSortThreads / 32) * R; i += kSortThreads) (&s_peer[0][0])[i] = 0u;
   for (;;) {
     if (tid == 0) s_tile = atomicAdd(tile_counter, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile >= nblk) break;
-#pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) s_whist[w][tid] = 0;
+    for (int i = tid; i < (kSortThreads / 32) * R; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
     __syncthreads();
 
     const uint32_t seg = tile * kSortTile + (uint32_t)warp * (32 * kSortItems) + lane;
@@ -261,7 +299,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
       const bool valid = seg + it * 32 < count;
-      const uint32_t d = (key[it] >> shift) & 255u;
+      const uint32_t d = (key[it] >> shift) & kMask;
       // peers with the same digit: each lane sets its bit in the digit's mask
       if (valid) atomicOr(&s_peer[warp][d], 1u << lane);
       __syncwarp();
@@ -278,61 +316,60 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
       loc[it] = base + rank;
     }
     __syncthreads();
-    // per digit (thread tid): exclusive prefix over warps and the tile total
-    uint32_t total = 0;
+    // per digit: exclusive prefix over warps and the tile total
+    uint32_t total[DPT], bex[DPT];
 #pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) {
-      const uint32_t c = s_whist[w][tid];
-      s_whist[w][tid] = total;
-      total += c;
-    }
-    // start of digit tid inside the tile: exclusive scan of the totals
-    {
-      uint32_t x = total;
+    for (int q = 0; q < DPT; ++q) {
+      const int d = tid * DPT + q;
+      uint32_t t = 0;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+      for (int w = 0; w < kSortThreads / 32; ++w) {
+        const uint32_t c = s_whist[w][d];
+        s_whist[w][d] = t;
+        t += c;
       }
-      if (lane == 31) s_wsum[warp] = x;
-      __syncthreads();
-      uint32_t wpre = 0;
-      for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
-      s_bexcl[tid] = wpre + x - total;
+      total[q] = t;
     }
-    // decoupled look-back for digit `tid`
-    uint32_t* my = look + (size_t)tile * 256 + tid;
-    uint32_t excl = 0;
-    if (tile == 0) {
-      atomicExch(my, kFlagInc | total);
-    } else {
-      atomicExch(my, kFlagAgg | total);
-      int64_t j = (int64_t)tile - 1;
-      while (j >= 0) {
-        volatile uint32_t* pj = look + j * 256 + tid;
-        uint32_t v = *pj;
-        int spins = 0;
-        while ((v & ~kCountMask) == 0u) {
-          if (++spins > kSpinLimit) {
-            set_status(status, BETA_ERR_TIMEOUT);
-            break;
+    // start of each digit inside the tile: exclusive scan of the totals
+    block_scan_digits<DPT>(total, bex, s_wsum);
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = tid * DPT + q;
+      s_bexcl[d] = bex[q];
+      // decoupled look-back for digit d
+      uint32_t* my = look + (size_t)tile * R + d;
+      uint32_t excl = 0;
+      if (tile == 0) {
+        atomicExch(my, kFlagInc | total[q]);
+      } else {
+        atomicExch(my, kFlagAgg | total[q]);
+        int64_t j = (int64_t)tile - 1;
+        while (j >= 0) {
+          volatile uint32_t* pj = look + j * R + d;
+          uint32_t v = *pj;
+          int spins = 0;
+          while ((v & ~kCountMask) == 0u) {
+            if (++spins > kSpinLimit) {
+              set_status(status, BETA_ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(64);
+            v = *pj;
           }
-          __nanosleep(64);
-          v = *pj;
+          excl += v & kCountMask;
+          if ((v & ~kCountMask) != kFlagAgg) break;  // inclusive prefix (or timeout)
+          --j;
         }
-        excl += v & kCountMask;
-        if ((v & ~kCountMask) != kFlagAgg) break;  // inclusive prefix (or timeout)
-        --j;
+        atomicExch(my, kFlagInc | (excl + total[q]));
       }
-      atomicExch(my, kFlagInc | (excl + total));
+      s_gbase[d] = s_gexcl[d] + excl;
     }
-    s_gbase[tid] = s_gexcl[tid] + excl;
     __syncthreads();
     // keys to their place inside the tile; loc becomes the tile position
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
       if (seg + it * 32 < count) {
-        const uint32_t d = (key[it] >> shift) & 255u;
+        const uint32_t d = (key[it] >> shift) & kMask;
         loc[it] += s_bexcl[d] + s_whist[warp][d];
         s_key[loc[it]] = key[it];
       }
@@ -349,7 +386,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_onesweep(
 #pragma unroll 4
     for (int i = tid; i < n_here; i += kSortThreads) {
       const uint32_t k = s_key[i];
-      const uint32_t d = (k >> shift) & 255u;
+      const uint32_t d = (k >> shift) & kMask;
       const uint32_t gpos = s_gbase[d] + ((uint32_t)i - s_bexcl[d]);
       if (write_keys) keys_out[gpos] = k;
       vals_out[gpos] = s_val[i];
@@ -529,15 +566,19 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
   SortWs w = carve(ws, n_items, cap, total_tiles);
   const int64_t nblk_d = cdiv(n_items, kSortTile);
   const int64_t nblk_t = cdiv(cap > 0 ? cap : 1, kSortTile);
-  const int np_t = tile_passes(total_tiles);
+  const TilePlan tp = tile_plan(total_tiles);
+  const int np_t = tp.passes, rt = 1 << tp.bits;
   const int persist = sm_count() * 4;
   uint32_t* gh_d = w.ghist;
-  uint32_t* gh_t = w.ghist + kMaxPasses * 256;
+  uint32_t* gh_t = w.ghist + kMaxPasses * 512;
 
-  static bool smem_set = false;   // 32 KB dynamic + ~20 KB static shared memory per CTA
+  // 32 KB dynamic + 20 / 38 KB static shared memory per CTA (8 / 9-bit digits)
+  static bool smem_set = false;
   if (!smem_set) {
-    if (cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kOnesweepSmem) != cudaSuccess ||
-        cudaFuncSetAttribute(k_onesweep, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_onesweep<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOnesweepSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_onesweep<8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess ||
+        cudaFuncSetAttribute(k_onesweep<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOnesweepSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_onesweep<9>, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
       return cudaGetLastError();
     smem_set = true;
   }
@@ -546,8 +587,8 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
   // 1. stable sort of all records by depth key (4 passes of 8 bits)
   int grid_h = (int)std::min<int64_t>(cdiv(n_items, 4 * kSortThreads * kHistVec), (int64_t)persist * 2);
   if (grid_h < 1) grid_h = 1;
-  k_digit_hist<<<grid_h, kSortThreads, 0, s>>>(pb.key, n_items, nullptr, n_items, 4, gh_d, w.look_d,
-                                               nblk_d);
+  k_digit_hist<8, kMaxPasses><<<grid_h, kSortThreads, 0, s>>>(pb.key, n_items, nullptr, n_items, 4, gh_d,
+                                                               w.look_d, nblk_d);
   const uint32_t* kin = pb.key;
   const uint32_t* vin = nullptr;
   uint32_t* kbuf[2] = {w.dkey_a, w.dkey_b};
@@ -555,7 +596,7 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
   int grid_d = (int)std::min<int64_t>(nblk_d, persist);
   if (grid_d < 1) grid_d = 1;
   for (int p = 0; p < 4; ++p) {
-    k_onesweep<<<grid_d, kSortThreads, kOnesweepSmem, s>>>(kin, vin, kbuf[p & 1], vbuf[p & 1], p < 3 ? 1 : 0,
+    k_onesweep<8><<<grid_d, kSortThreads, kOnesweepSmem, s>>>(kin, vin, kbuf[p & 1], vbuf[p & 1], p < 3 ? 1 : 0,
                                                gh_d + p * 256, w.look_d + (size_t)p * nblk_d * 256,
                                                w.counters + p, n_items, nullptr, n_items, 8 * p,
                                                d_status);
@@ -579,8 +620,12 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
   if (np_t > 0) {
     int grid_th = (int)std::min<int64_t>(cdiv(cap, 4 * kSortThreads * kHistVec), (int64_t)persist * 2);
     if (grid_th < 1) grid_th = 1;
-    k_digit_hist<<<grid_th, kSortThreads, 0, s>>>(w.pkey_a, 0, d_count, cap, np_t, gh_t, w.look_t,
-                                                  nblk_t);
+    if (tp.bits == 9)
+      k_digit_hist<9, 2><<<grid_th, kSortThreads, 0, s>>>(w.pkey_a, 0, d_count, cap, np_t, gh_t, w.look_t,
+                                                          nblk_t);
+    else
+      k_digit_hist<8, kMaxPasses><<<grid_th, kSortThreads, 0, s>>>(w.pkey_a, 0, d_count, cap, np_t, gh_t,
+                                                                   w.look_t, nblk_t);
     int grid_t = (int)std::min<int64_t>(nblk_t, persist);
     if (grid_t < 1) grid_t = 1;
     uint32_t* pk[2] = {w.pkey_b, w.pkey_a};
@@ -588,10 +633,11 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
     const uint32_t* ki = w.pkey_a;
     const uint32_t* vi = pval_emit;
     for (int p = 0; p < np_t; ++p) {
-      k_onesweep<<<grid_t, kSortThreads, kOnesweepSmem, s>>>(ki, vi, pk[p & 1], pv[p & 1], 1,
-                                                 gh_t + p * 256, w.look_t + (size_t)p * nblk_t * 256,
-                                                 w.counters + kMaxPasses + p, 0, d_count, cap, 8 * p,
-                                                 d_status);
+      auto k = tp.bits == 9 ? k_onesweep<9> : k_onesweep<8>;
+      k<<<grid_t, kSortThreads, kOnesweepSmem, s>>>(ki, vi, pk[p & 1], pv[p & 1], 1, gh_t + p * rt,
+                                                     w.look_t + (size_t)p * nblk_t * rt,
+                                                     w.counters + kMaxPasses + p, 0, d_count, cap,
+                                                     tp.bits * p, d_status);
       ki = pk[p & 1];
       vi = pv[p & 1];
     }

@@ -77,6 +77,23 @@ def test_bin_sort_bit_exact_mixed_view_batch():
     assert K > 0
 
 
+@pytest.mark.parametrize("cfg,n_views,tile,bits", [(3, 16, 16, 17), (5, 8, 16, 18), (5, 8, 8, 20)])
+def test_bin_sort_bit_exact_wide_tile_ids(cfg, n_views, tile, bits):
+    """Tile ids of 17-18 bits take two 9-bit passes, wider ones three 8-bit
+    passes: both orderings equal the oracle's bit for bit."""
+    sc = scenes.config_scene(cfg, n=20_000, n_views=n_views)
+    opts = _lib.default_opts(tile_w=tile, tile_h=tile)
+    total = sum(((c.width + tile - 1) // tile) * ((c.height + tile - 1) // tile) for c in sc.cameras)
+    assert (total - 1).bit_length() == bits
+    rast, _ = gc.rasterize(sc.planes, sc.n, sc.n_lobes, sc.cameras, opts=opts)
+    K, ranges, vals = gc.sorted_pairs(rast)
+    _, recs, oranges = oracle.bin_pairs(sc.planes, sc.n, sc.n_lobes, sc.cameras, tile_w=tile, tile_h=tile,
+                                        pitch=sc.pitch)
+    assert K == len(recs) and K > 0
+    assert np.array_equal(ranges, oranges)
+    assert np.array_equal(vals, recs)
+
+
 def test_bin_sort_ragged_sizes():
     for n in (1, 3, 4095, 4096, 4097, 9000):
         sc = scenes.config_scene(1, n=n, seed=11)
