@@ -182,6 +182,29 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
   }
 }
 
+// Per-view geometry for the backward: the same quantities as the rule chain
+// (A = W Rq, J, M = J A S), at ordinary fp32 speed -- no tile rectangle: a
+// record only holds 2D gradients if it was binned, so its rectangle was
+// non-empty.
+__device__ __forceinline__ void view_geo_bwd(const PrimGeo& pg, const ViewDev& V, ViewGeo& g) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      g.A[r * 3 + c] = fmaf(V.R[r * 3 + 0], pg.Rq[0 * 3 + c],
+                            fmaf(V.R[r * 3 + 1], pg.Rq[1 * 3 + c], V.R[r * 3 + 2] * pg.Rq[2 * 3 + c]));
+  g.iz = __frcp_rn(g.tc[2]);
+  g.j00 = V.fx * g.iz;
+  g.j11 = V.fy * g.iz;
+  g.j02 = -(g.j00 * g.tc[0]) * g.iz;
+  g.j12 = -(g.j11 * g.tc[1]) * g.iz;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    g.M0[c] = fmaf(g.j00, g.A[0 * 3 + c], g.j02 * g.A[2 * 3 + c]) * pg.s[c];
+    g.M1[c] = fmaf(g.j11, g.A[1 * 3 + c], g.j12 * g.A[2 * 3 + c]) * pg.s[c];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // backward: 2D gradients (d mu', d Sigma' (a, b, c), d o, d beta, d colour)
 // of every view -> gradients of the raw parameters.  Gradients w.r.t. the
@@ -234,9 +257,9 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict_
       g2[1] = z4;
       g2[2] = z4;
       ViewGeo g;
-      int rc[4];
       uint32_t kk;
-      if (!rule_depth(pg, V, g, kk) || !rule_view(pg, V, ro.blur_eps, ro.tile_w, ro.tile_h, g, rc)) continue;
+      if (!rule_depth(pg, V, g, kk)) continue;
+      view_geo_bwd(pg, V, g);
       // whitening of Sigma' (the forward's formulas) turns the whitened sums
       // into d mu' and d Sigma' = [[ga, gb/2], [gb/2, gc]] (gb: off-diagonal scalar)
       float gmx, gmy, ga, gb, gc;
@@ -250,8 +273,8 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict_
         float det = fmaf(m01, m01, fmaf(m02, m02, m12 * m12));
         const float aa = a0 + ro.blur_eps;
         if (ro.blur_eps != 0.0f) det = fmaf(ro.blur_eps, a0 + c0 + ro.blur_eps, det);
-        const float sa = sqrtf(aa), sd = sqrtf(det);
-        const float p = 1.0f / sa, q1 = sa / sd, q2 = -(bb * p) / sd;
+        const float p = rsqrtf(aa), isd = rsqrtf(det);
+        const float q1 = (aa * p) * isd, q2 = -(bb * p) * isd;
         const float b2 = 2.0f * at.beta;
         gmx = b2 * fmaf(p, G[0], q2 * G[1]);
         gmy = b2 * q1 * G[1];
@@ -310,8 +333,7 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict_
       }
       if (M > 0 && ro.color_mode != 1) {
         float vx = p[0] - V.campos[0], vy = p[1] - V.campos[1], vz = p[2] - V.campos[2];
-        float len = sqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
-        float il = 1.0f / len;
+        float il = rsqrtf(fmaf(vx, vx, fmaf(vy, vy, vz * vz)));
         vx *= il;
         vy *= il;
         vz *= il;
@@ -323,15 +345,17 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict_
           const float rx = at.lobe_dir[m][0], ry = at.lobe_dir[m][1], rz = at.lobe_dir[m][2];
           float dot = rx * vx + ry * vy + rz * vz;
           if (dot > 0.0f) {
+            // w = dot^bm and d w / d dot = bm w / dot, with the MUFU log2/exp2
+            // (relative error ~1e-6, far inside the gradient tolerance)
             float bm = at.lobe_beta[m];
-            float lw = log2f(dot);
-            float wgt = exp2f(bm * lw);
+            float lw = lg2_approx(dot);
+            float wgt = ex2_approx(bm * lw);
             dL[3] += wgt * gr;
             dL[4] += wgt * gg;
             dL[5] += wgt * gbl;
             float gw = gr * L[3] + gg * L[4] + gbl * L[5];
             dL[2] += gw * wgt * (lw * kLn2) * bm;
-            float ddot = gw * bm * exp2f((bm - 1.0f) * lw);
+            float ddot = gw * bm * wgt * __frcp_rn(dot);
             dRm[m][0] += ddot * vx;
             dRm[m][1] += ddot * vy;
             dRm[m][2] += ddot * vz;
