@@ -361,31 +361,75 @@ def main():
         del singles, gview
 
         # ---- end to end through host buffers --------------------------------
+        # Every step copies its inputs (parameters, targets) from pinned host
+        # memory and reads its results (gradients, losses) back, inside the
+        # timed region.  The copies run on a second stream and are pipelined
+        # with the compute: step i+1's inputs land in a staging buffer while
+        # step i runs, and step i's results leave from a staging buffer while
+        # step i+1 runs.
         h_planes = torch.from_numpy(sc.planes).pin_memory()
         h_target = torch.from_numpy(np.concatenate([t.reshape(-1) for t in targets_np])).pin_memory()
         h_grad = torch.empty(planes.shape, dtype=torch.float32).pin_memory()
         h_loss = torch.empty(V, dtype=torch.float32).pin_memory()
+        cstream = torch.cuda.Stream()
+        st_p = [torch.empty_like(planes) for _ in range(2)]
+        st_t = [torch.empty_like(target) for _ in range(2)]
+        st_g = [torch.empty_like(grad) for _ in range(2)]
+        st_l = [torch.empty_like(rast.loss) for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_free = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+        ev_sent = [torch.cuda.Event() for _ in range(2)]
+        for e in ev_free + ev_sent:
+            e.record(stream)
 
-        def step_e2e():
-            planes.copy_(h_planes, non_blocking=True)
-            target.copy_(h_target, non_blocking=True)
+        def h2d(i):
+            b = i % 2
+            with torch.cuda.stream(cstream):
+                cstream.wait_event(ev_free[b])
+                st_p[b].copy_(h_planes, non_blocking=True)
+                st_t[b].copy_(h_target, non_blocking=True)
+                ev_in[b].record(cstream)
+
+        def step_e2e(i, n):
+            b = i % 2
+            stream.wait_event(ev_in[b])
+            planes.copy_(st_p[b])
+            target.copy_(st_t[b])
+            ev_free[b].record(stream)
+            if i + 1 < n:
+                h2d(i + 1)
             step()
-            h_grad.copy_(grad, non_blocking=True)
-            h_loss.copy_(rast.loss, non_blocking=True)
+            stream.wait_event(ev_sent[b])
+            st_g[b].copy_(grad)
+            st_l[b].copy_(rast.loss)
+            ev_out[b].record(stream)
+            with torch.cuda.stream(cstream):
+                cstream.wait_event(ev_out[b])
+                h_grad.copy_(st_g[b], non_blocking=True)
+                h_loss.copy_(st_l[b], non_blocking=True)
+                ev_sent[b].record(cstream)
 
-        for _ in range(args.warmup):
-            step_e2e()
+        h2d(0)
+        for i in range(args.warmup):
+            step_e2e(i, args.warmup)
+        stream.wait_stream(cstream)
+        torch.cuda.synchronize()
         barrier()
         e0.record(stream)
-        for _ in range(args.steps):
-            step_e2e()
+        h2d(0)
+        for i in range(args.steps):
+            step_e2e(i, args.steps)
+        stream.wait_stream(cstream)
         e1.record(stream)
+        torch.cuda.synchronize()
         barrier()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1)) / args.steps
         extras["e2e"] = {"value": pix_per_step / (ms_e2e * 1e-3) / 1e6, "unit": UNIT,
                          "h2d_bytes_per_step": (h_planes.numel() + h_target.numel()) * 4 * world,
                          "d2h_bytes_per_step": (h_grad.numel() + h_loss.numel()) * 4 * world,
-                         "ms_per_step": ms_e2e}
+                         "ms_per_step": ms_e2e, "copies": "pipelined on a second stream"}
+        del st_p, st_t, st_g, st_l
 
         # ---- the oracle on the host cores (bounded sample) -------------------
         if rank == 0 and world == 1:
@@ -394,9 +438,13 @@ def main():
                                       "sample": f"{args.cpu_pixels} seeded pixels of view 0 of the same "
                                                 f"workload, forward only (FP64, every Beta per pixel), {tot:.1f} s"}
 
-    # kernel launches of ours inside the timed region (all inside the replayed graph)
-    np_t = math.ceil(math.ceil(math.log2(max(rast.total_tiles, 2))) / 8)
-    per_step = (1 + (1 + 1 + 4 + 3 + (1 + np_t if np_t > 0 else 0) + 1) + (3 if rast.persistent else 0)
+    # kernel launches of ours inside the timed region (all inside the replayed graph):
+    # project 1; bin_sort: prep, depth histogram, 4 depth passes, emit, tile
+    # histogram + tile passes (two 9-bit passes for 17-18-bit tile ids), tile
+    # ranges; schedule 3 (persistent); raster fwd 1; L1 2; raster bwd 1; project bwd 1
+    tbits = max(1, math.ceil(math.log2(max(rast.total_tiles, 2))))
+    np_t = 2 if tbits in (17, 18) else math.ceil(tbits / 8)
+    per_step = (1 + (1 + 1 + 4 + 1 + (1 + np_t) + 1) + (3 if rast.persistent else 0)
                 + 1 + 2 + 1 + 1)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

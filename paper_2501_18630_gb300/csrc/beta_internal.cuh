@@ -260,6 +260,11 @@ __device__ __forceinline__ dd dd_div(dd a, dd b) {
   float q2 = __fdiv_rn(r, b.hi);
   return fast_two_sum(q, q2);
 }
+// a * b in double-float
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  dd p = two_prod(a.hi, b.hi);
+  return fast_two_sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
+}
 __device__ __forceinline__ dd dd_mul_f(dd a, float b) {
   dd p = two_prod(a.hi, b);
   return fast_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));

@@ -138,8 +138,9 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
     if (bin) {
       // projected centre in double-float
       dd tx = cam_coord_dd(V, 0, pg.mu), ty = cam_coord_dd(V, 1, pg.mu), tz = cam_coord_dd(V, 2, pg.mu);
-      dd mx = dd_add_f(dd_mul_f(dd_div(tx, tz), V.fx), V.cx);
-      dd my = dd_add_f(dd_mul_f(dd_div(ty, tz), V.fy), V.cy);
+      const dd rz = dd_div(dd{1.0f, 0.0f}, tz);   // one double-float division for both axes
+      dd mx = dd_add_f(dd_mul_f(dd_mul(tx, rz), V.fx), V.cx);
+      dd my = dd_add_f(dd_mul_f(dd_mul(ty, rz), V.fy), V.cy);
       float ix = floorf(mx.hi), iy = floorf(my.hi);
       float fx = (mx.hi - ix) + mx.lo, fy = (my.hi - iy) + my.lo;
       if (fx < 0.0f) { ix -= 1.0f; fx += 1.0f; }
@@ -158,10 +159,9 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
       if (ro.blur_eps != 0.0f) det = fmaf(ro.blur_eps, a0 + c0 + ro.blur_eps, det);
       bin = (det > 0.0f) && (a > 0.0f) && isfinite(det);
       if (bin) {
-        float sa = sqrtf(a), sd = sqrtf(det);
-        float pp = 1.0f / sa;
-        float q1 = sa / sd;
-        float q2 = -(b * pp) / sd;
+        const float pp = rsqrtf(a), isd = rsqrtf(det);
+        const float q1 = (a * pp) * isd;
+        const float q2 = -(b * pp) * isd;
         float col[3];
         sb_colour<M>(p, at, V, ro.color_mode, col);
         o0 = make_float4(ix, iy, 0.5f - fx, 0.5f - fy);
