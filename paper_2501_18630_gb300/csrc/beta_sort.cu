@@ -425,6 +425,7 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
   return pre + inc - x;
 }
 
+constexpr int kEmitStage = 4096;   // pairs staged in shared memory per emit block (32 KB)
 constexpr unsigned long long kEAgg = 1ull << 62, kEInc = 2ull << 62, kECount = (1ull << 62) - 1;
 
 // Pair counts of the records in depth order, their exclusive scan and the
@@ -443,6 +444,7 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
   __shared__ unsigned long long s_w[kSortThreads / 32];
   __shared__ unsigned long long s_base;
   __shared__ uint32_t s_blk;
+  __shared__ uint32_t s_pk[kEmitStage], s_pv[kEmitStage];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
   __syncthreads();
@@ -504,7 +506,11 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
     }
   }
   __syncthreads();
-  unsigned long long off = s_base + excl;
+  // pairs land in shared memory first (the block's first kEmitStage pairs),
+  // then leave with coalesced stores; pairs past the stage (blocks of very
+  // large primitives) are written directly
+  const unsigned long long bbase = s_base;
+  unsigned long long off = excl;   // relative to the block's first pair
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     const uint32_t c = rect_count(rc[k]);
@@ -515,12 +521,24 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const uint32_t* __restric
     const int ty0 = (int)(rc[k].y & 0xffffu), ty1 = (int)(rc[k].y >> 16);
     for (int ty = ty0; ty <= ty1; ++ty)
       for (int tx = tx0; tx <= tx1; ++tx) {
-        if ((int64_t)off < cap) {
-          pkey[off] = (uint32_t)(toff + ty * ntx + tx);
-          pval[off] = rec[k];
+        const uint32_t key = (uint32_t)(toff + ty * ntx + tx);
+        if (off < (unsigned long long)kEmitStage) {
+          s_pk[off] = key;
+          s_pv[off] = rec[k];
+        } else if ((int64_t)(bbase + off) < cap) {
+          pkey[bbase + off] = key;
+          pval[bbase + off] = rec[k];
         }
         ++off;
       }
+  }
+  __syncthreads();
+  const int n_stage = (int)min(total, (unsigned long long)kEmitStage);
+  for (int i = threadIdx.x; i < n_stage; i += kSortThreads) {
+    if ((int64_t)(bbase + i) < cap) {
+      pkey[bbase + i] = s_pk[i];
+      pval[bbase + i] = s_pv[i];
+    }
   }
 }
 
