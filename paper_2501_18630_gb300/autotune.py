@@ -18,8 +18,8 @@ from .batched import BatchedStep
 
 # (tile_w, tile_h, batch_s, persistent)
 CANDIDATES = [
-    (16, 16, 256, True), (16, 16, 128, True), (16, 16, 64, True), (16, 16, 256, False),
-    (16, 8, 128, True), (16, 8, 64, True), (32, 16, 256, True), (8, 8, 64, True),
+    (16, 16, 256, False), (16, 16, 256, True), (16, 16, 128, True), (16, 8, 128, False),
+    (16, 8, 128, True), (16, 8, 64, False), (8, 8, 64, False), (32, 16, 256, True),
 ]
 
 
@@ -32,7 +32,7 @@ def cache_path() -> str:
 
 def workload_key(n: int, n_lobes: int, cameras, device) -> str:
     res = ",".join(f"{c.width}x{c.height}" for c in cameras)
-    return f"n={n};M={n_lobes};views={res};dev={torch.cuda.get_device_name(device)}"
+    return f"v2;n={n};M={n_lobes};views={res};dev={torch.cuda.get_device_name(device)}"
 
 
 def _load():

@@ -8,18 +8,19 @@
 // stopping before a primitive once T < t_eps.
 //
 // Layout: one CTA per TW x TH tile, one pixel per thread; warp w owns an 8x4
-// pixel block.  Records are staged S at a time in shared memory together with
-// a mask of the warp blocks their support ellipse can reach (an exact
-// ellipse-vs-rectangle test); each warp walks only the records of its mask
-// bit (ballot over 32 records), so whole warps skip records that cannot touch
-// them.  Transmittance early exit is decided per warp (__all_sync) and per
-// CTA (__syncthreads_or).
+// pixel block.  Records of the tile's list are staged S at a time in shared
+// memory (double-buffered cp.async, one batch ahead); each warp tests 32
+// staged records at a time against its block (an exact ellipse-vs-rectangle
+// test, one record per lane) and walks only the hits (ballot), so whole warps
+// skip records that cannot touch them.  Transmittance early exit is decided
+// per warp (__all_sync) and per CTA (__syncthreads_or).
 //
 // Backward: the same tiling walks each tile list from the largest
 // last-contributor position down, recovering T_k = T_{k+1} / (1 - alpha_k)
 // and the suffix colour S (as g . S), and produces per-record 2D gradients
-// (d mu', d Sigma', d o, d beta, d colour); a warp sums its lanes' ten values
-// with a 12-shuffle reduce-scatter and issues one atomic per value.
+// (d mu', d Sigma', d o, d beta, d colour): up to 12 active lanes add their
+// ten values with three 16-byte vector atomics each, otherwise the warp sums
+// them with a 12-shuffle reduce-scatter and issues one atomic per value.
 //
 // Scheduling: with a schedule buffer (beta_schedule) the raster kernels are
 // persistent -- a grid sized to the SMs takes tiles from a global counter in
