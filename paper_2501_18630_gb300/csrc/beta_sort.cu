@@ -31,6 +31,7 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr int kSpinLimit = 1 << 20;
+constexpr int kLookWin = 8;   // look-back predecessors loaded per round
 constexpr int kMaxPasses = 4;
 constexpr int kOnesweepSmem = 2 * kSortTile * 4;  // staged keys + values (32 KB)
 
@@ -332,35 +333,47 @@ __global__ void __launch_bounds__(kSortThreads, BITS == 8 ? 4 : 3) k_onesweep(
     }
     // start of each digit inside the tile: exclusive scan of the totals
     block_scan_digits<DPT>(total, bex, s_wsum);
+    // post this tile's count of each of the thread's digits: the inclusive
+    // prefix for tile 0, the tile's own aggregate otherwise
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
       const int d = tid * DPT + q;
       s_bexcl[d] = bex[q];
-      // decoupled look-back for digit d
-      uint32_t* my = look + (size_t)tile * R + d;
+      atomicExch(look + (size_t)tile * R + d, (tile == 0 ? kFlagInc : kFlagAgg) | total[q]);
+    }
+    // decoupled look-back, kLookWin predecessors per round: the loads of a
+    // round are independent, so a chain of aggregates (the first wave of
+    // tiles all post theirs at once) costs one latency per kLookWin tiles
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+      const int d = tid * DPT + q;
       uint32_t excl = 0;
-      if (tile == 0) {
-        atomicExch(my, kFlagInc | total[q]);
-      } else {
-        atomicExch(my, kFlagAgg | total[q]);
-        int64_t j = (int64_t)tile - 1;
-        while (j >= 0) {
-          volatile uint32_t* pj = look + j * R + d;
-          uint32_t v = *pj;
-          int spins = 0;
-          while ((v & ~kCountMask) == 0u) {
-            if (++spins > kSpinLimit) {
-              set_status(status, BETA_ERR_TIMEOUT);
-              break;
+      if (tile > 0) {
+        for (int64_t j = (int64_t)tile - 1;; j -= kLookWin) {
+          uint32_t v[kLookWin];
+#pragma unroll
+          for (int i = 0; i < kLookWin; ++i)
+            v[i] = j - i >= 0 ? *(volatile const uint32_t*)(look + (j - i) * R + d) : kFlagInc;
+          bool stop = false;
+#pragma unroll
+          for (int i = 0; i < kLookWin; ++i) {
+            if (stop) break;
+            int spins = 0;
+            while ((v[i] & ~kCountMask) == 0u) {   // not posted yet
+              if (++spins > kSpinLimit) {
+                set_status(status, BETA_ERR_TIMEOUT);
+                v[i] = kFlagInc;
+                break;
+              }
+              __nanosleep(64);
+              v[i] = *(volatile const uint32_t*)(look + (j - i) * R + d);
             }
-            __nanosleep(64);
-            v = *pj;
+            excl += v[i] & kCountMask;
+            stop = (v[i] & ~kCountMask) != kFlagAgg;   // an inclusive prefix ends the walk
           }
-          excl += v & kCountMask;
-          if ((v & ~kCountMask) != kFlagAgg) break;  // inclusive prefix (or timeout)
-          --j;
+          if (stop) break;
         }
-        atomicExch(my, kFlagInc | (excl + total[q]));
+        atomicExch(look + (size_t)tile * R + d, kFlagInc | (excl + total[q]));
       }
       s_gbase[d] = s_gexcl[d] + excl;
     }
