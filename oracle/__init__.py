@@ -82,6 +82,8 @@ def lib():
                                          ctypes.POINTER(OCam), ctypes.POINTER(OOpts), ctypes.POINTER(OPrim)]
             L.oracle_rule_exp.restype = ctypes.c_float
             L.oracle_rule_exp.argtypes = [ctypes.c_float]
+            L.oracle_rule_opacity.restype = None
+            L.oracle_rule_opacity.argtypes = [fp, ctypes.c_int32, fp]
             L.oracle_rule_rects.restype = None
             L.oracle_rule_rects.argtypes = [fp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.POINTER(OCam), ctypes.c_float, ctypes.c_float,
@@ -177,6 +179,15 @@ def project(planes, n, n_lobes, cam, **opts):
 
 def rule_exp(x: float) -> float:
     return float(lib().oracle_rule_exp(ctypes.c_float(x)))
+
+
+def rule_opacity(logit) -> np.ndarray:
+    """The fixed fp32 opacity rule of the relocation step (float32 array)."""
+    x = np.ascontiguousarray(np.asarray(logit, np.float32))
+    out = np.empty_like(x)
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib().oracle_rule_opacity(x.ctypes.data_as(fp), int(x.size), out.ctypes.data_as(fp))
+    return out
 
 
 def rule_rects(planes, n, n_lobes, cam, blur_eps=0.0, tile_w=16, tile_h=16, b_lo=-np.inf, b_hi=np.inf):

@@ -354,6 +354,21 @@ float oracle_rule_exp(float x) {
   return p * scale;
 }
 
+/* Opacity by a fixed fp32 rule, for the relocation step's decisions (Sec. 3.4
+ * Densification: dead primitives and sampling weights):
+ * o = 1 / (1 + rule_exp(-x)), x = the logit clamped to [-80, 80] (NaN -> -80),
+ * every operation rounded to nearest in float. */
+void oracle_rule_opacity(const float* logit, int32_t n, float* o) {
+  for (int32_t i = 0; i < n; ++i) {
+    float x = logit[i];
+    if (!(x >= -80.0f)) x = -80.0f;
+    if (x > 80.0f) x = 80.0f;
+    float e = oracle_rule_exp(-x);
+    float d = 1.0f + e;
+    o[i] = 1.0f / d;
+  }
+}
+
 /* Tile rectangle of primitive i under rule B1.  rect = (tx0, tx1, ty0, ty1),
  * inclusive tile indices, tx0 > tx1 when the primitive touches no tile.
  * Returns 1 if the primitive is binned, 0 otherwise.  key receives the

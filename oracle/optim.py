@@ -116,3 +116,54 @@ def adam_step(planes, grad, m, v, eta, n, n_lobes, lr, step, beta1=0.9, beta2=0.
         P[k, cols] -= lr[GROUPS[groups[k]]] * mh / (np.sqrt(vh) + eps)
     P[P_MEAN:P_MEAN + 3, cols] += noise
     return P, M, V, reg
+
+
+# ---------------------------------------------------------------------------
+# Relocation of dead primitives (Sec. 3.4 "Densification", Eq. eq:densify):
+# a primitive whose opacity is below min_opacity is dead; it is respawned as
+# a copy of a live primitive drawn by multinomial sampling with probabilities
+# proportional to opacity (with replacement, one draw per dead primitive, in
+# index order); a live primitive that ends up with N copies in total
+# (itself included) gets o' = 1 - (1 - o)^(1/N) on all of them, its other
+# parameters unchanged (opacity-only adjustment).  The copies' optimiser
+# moments are reset to zero.
+#
+# Decisions are integers: dead = rule_opacity(logit) < min_opacity with the
+# fixed fp32 rule, weight = floor(rule_opacity * 2^24) for live primitives,
+# inclusive cumulative sum W (64-bit integers); the caller's 32-bit random
+# word r picks t = floor(r W_total / 2^32) and the source is the first i with
+# W_i > t.  The new opacities are FP64.
+# ---------------------------------------------------------------------------
+
+def relocate(planes, m, v, rnd, n, min_opacity):
+    """Returns new (planes, m, v) (float64), the source index of every
+    primitive (-1: kept) and the number relocated."""
+    from . import rule_opacity
+    P = np.array(planes, np.float64)
+    Mo = np.array(m, np.float64)
+    Vo = np.array(v, np.float64)
+    src = np.full(n, -1, np.int64)
+    if n == 0:
+        return P, Mo, Vo, src, 0
+    o32 = rule_opacity(np.asarray(planes, np.float32)[P_OPACITY, :n])
+    dead = o32 < np.float32(min_opacity)
+    w = np.where(dead, 0, (o32 * np.float32(16777216.0)).astype(np.uint64)).astype(np.uint64)
+    cdf = np.cumsum(w, dtype=np.uint64)
+    total = int(cdf[-1])
+    if total == 0:
+        return P, Mo, Vo, src, 0
+    dead_idx = np.nonzero(dead)[0]
+    for d in dead_idx:
+        t = (int(rnd[d]) * total) >> 32
+        src[d] = int(np.searchsorted(cdf, np.uint64(t), side="right"))
+    copies = np.bincount(src[dead_idx], minlength=n) if len(dead_idx) else np.zeros(n, np.int64)
+    for s in np.nonzero(copies)[0]:
+        N = copies[s] + 1
+        o = 1.0 / (1.0 + math.exp(-P[P_OPACITY, s]))
+        o_new = -math.expm1(math.log1p(-o) / N)
+        P[P_OPACITY, s] = math.log(o_new) - math.log1p(-o_new)
+    for d in dead_idx:
+        P[:, d] = P[:, src[d]]
+        Mo[:, d] = 0.0
+        Vo[:, d] = 0.0
+    return P, Mo, Vo, src, len(dead_idx)

@@ -123,3 +123,65 @@ def test_noise_scale_is_the_beta_kernel_at_b_ln25():
     d = _noise_case(0.0, [1, 0, 0, 0], [0.0, 0.0, 0.0], [1.0, 0.0, 0.0])
     assert d[0] == pytest.approx(5e4 * 1.6e-4 * 2.0 ** -100, rel=1e-12)
     assert optim.beta_kernel(0.25, math.log(25.0)) == pytest.approx(0.75 ** 100, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# relocation (Sec. 3.4 Densification, Eq. eq:densify)
+# ---------------------------------------------------------------------------
+
+def _reloc_planes(logits):
+    n = len(logits)
+    p = np.zeros((NP, n))
+    p[optim.P_OPACITY] = logits
+    p[:3] = np.arange(3 * n).reshape(3, n)        # distinct positions identify copies
+    p[optim.P_QUAT] = 1.0
+    return p
+
+
+def test_relocation_preserves_the_combined_opacity():
+    # one live primitive (o = 0.3), two dead ones: three copies of o' with
+    # 1 - (1 - o')^3 = o (Eq. eq:densify at the centre, f = 1)
+    logit = math.log(0.3 / 0.7)
+    p = _reloc_planes([logit, -20.0, -20.0])
+    m = np.ones_like(p)
+    P, Mo, Vo, src, k = optim.relocate(p, m, m, np.array([1, 2**31, 2**32 - 1], np.uint64), 3, 0.005)
+    assert k == 2 and list(src) == [-1, 0, 0]
+    o_new = 1.0 / (1.0 + np.exp(-P[optim.P_OPACITY]))
+    assert np.allclose(o_new, o_new[0]) and 1.0 - (1.0 - o_new[0]) ** 3 == pytest.approx(0.3, rel=1e-12)
+    assert np.all(P[:3, 1] == p[:3, 0]) and np.all(P[:3, 2] == p[:3, 0])     # copies of the source
+    assert np.all(Mo[:, 1:] == 0) and np.all(Mo[:, 0] == 1) and np.all(Vo[:, 1:] == 0)
+
+
+def test_relocation_small_opacity_is_o_over_n():
+    # Taylor reading of the paper: o' = 1 - (1 - o)^(1/N) ~ o / N for small o
+    o = 0.01
+    p = _reloc_planes([math.log(o / (1 - o))] + [-30.0] * 4)
+    P, _, _, src, k = optim.relocate(p, np.zeros_like(p), np.zeros_like(p), np.zeros(5, np.uint64), 5, 0.005)
+    assert k == 4 and np.all(src[1:] == 0)
+    o_new = 1.0 / (1.0 + math.exp(-P[optim.P_OPACITY, 0]))
+    assert o_new == pytest.approx(o / 5, rel=o)                 # error O(o)
+    assert o_new == pytest.approx(1 - (1 - o) ** 0.2, rel=1e-12)
+
+
+def test_relocation_samples_in_proportion_to_opacity():
+    # live opacities 0.1 / 0.3 / 0.6; random words spread uniformly over
+    # [0, 2^32): the draws are non-decreasing in the word and hit each source
+    # in proportion to its opacity
+    lo = [math.log(x / (1 - x)) for x in (0.1, 0.3, 0.6)]
+    nd = 2000
+    p = _reloc_planes(lo + [-30.0] * nd)
+    rnd = (np.arange(nd, dtype=np.uint64) * (2**32 // nd)).astype(np.uint64)
+    rr = np.concatenate([np.zeros(3, np.uint64), rnd])
+    _, _, _, src, k = optim.relocate(p, np.zeros_like(p), np.zeros_like(p), rr, 3 + nd, 0.005)
+    assert k == nd and np.all(np.diff(src[3:]) >= 0)
+    frac = np.bincount(src[3:], minlength=3) / nd
+    assert np.allclose(frac, [0.1, 0.3, 0.6], atol=1e-3)
+
+
+def test_relocation_without_dead_or_live_primitives_is_identity():
+    p = _reloc_planes([0.0, 1.0, 2.0])
+    P, _, _, src, k = optim.relocate(p, np.zeros_like(p), np.zeros_like(p), np.zeros(3, np.uint64), 3, 0.005)
+    assert k == 0 and np.all(src == -1) and np.array_equal(P, p)
+    p = _reloc_planes([-30.0, -40.0])
+    P, _, _, src, k = optim.relocate(p, np.zeros_like(p), np.zeros_like(p), np.zeros(2, np.uint64), 2, 0.005)
+    assert k == 0 and np.array_equal(P, p)
