@@ -243,6 +243,83 @@ int beta_project_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_
                      const beta_opts* opt, float* grad2d, float* grad_planes,
                      const int32_t* d_status, beta_stream_t stream);
 
+/* ---- the optimiser step after the backward (Sec. 3.4) ----------------- */
+
+/* Options of beta_adam_step (host struct).  beta_adam_default_opts() fills the
+ * appendix "Hyperparameters" values: lr = {1.6e-4 (mean, the initial
+ * lambda_lr; the caller applies its decay), 5e-3 (log-scale), 1e-3
+ * (quaternion), 5e-2 (opacity logit), 1e-3 (b), 2.5e-3 (c0), 2.5e-3 (lobe
+ * direction theta, phi), 2.5e-3 (lobe b_m), 2.5e-3 (lobe colour)},
+ * lambda_o = lambda_Sigma = 0.01, lambda_eps = 5e4, b' = ln 25; Adam
+ * beta1 0.9, beta2 0.999, eps 1e-15 (the paper does not state them). */
+typedef struct {
+  float lr[9];
+  float beta1, beta2, eps;
+  float lambda_o, lambda_sigma; /* regulariser weights of the composite loss          */
+  float lambda_eps, noise_b;    /* position-noise weight and the Beta kernel's b'     */
+  int32_t step;                 /* Adam step t >= 1 (bias correction 1 - beta^t)     */
+} beta_adam_opts;
+
+void beta_adam_default_opts(beta_adam_opts* opt /* host */);
+
+/* One optimiser step on the first n primitives (Sec. 3.4 "Optimization" and
+ * the composite loss):
+ *   g  = grad + lambda_o d(sum |o|) + lambda_Sigma d(sum_j sqrt(eig_j Sigma))
+ *        (= lambda_o o (1 - o) on the opacity logit, lambda_Sigma s_j on log-scale j)
+ *   Adam with one learning rate per parameter group (lr[] above),
+ *   mu += lambda_eps lr[0] (1 - o)^(4 e^b') Sigma eta,  Sigma = R diag(s^2) R^T,
+ * with o, s, R taken before the step.
+ *   planes     [15 + 6M][pitch] in/out: raw parameters (beta_params layout)
+ *   grad       [15 + 6M][pitch] in: dL/d(raw parameters) (beta_project_bwd's output)
+ *   adam_m, adam_v [15 + 6M][pitch] in/out: moments (zero before the first step)
+ *   eta        [3][pitch] in: standard normal samples, one triple per primitive
+ *   reg_loss   device double[2] or NULL: lambda_o sum o and lambda_Sigma sum_j s_j
+ *              are ADDED to it
+ * All device pointers 16-byte aligned.  Returns BETA_ERR_ARG for null pointers,
+ * n > pitch, pitch not a multiple of 4, n_lobes > 8, step < 1, or betas outside
+ * [0, 1). */
+int beta_adam_step(int32_t n, int32_t pitch, int32_t n_lobes, float* planes, const float* grad,
+                   float* adam_m, float* adam_v, const float* eta, const beta_adam_opts* opt,
+                   double* reg_loss, beta_stream_t stream);
+
+/* Relocation of dead primitives (Sec. 3.4 "Densification", Eq. eq:densify),
+ * run every few hundred steps.  Primitive i < n is dead when its opacity,
+ * by the fixed fp32 rule o = 1 / (1 + e(-clamp(logit, -80, 80))) (e: the
+ * Cody-Waite / degree-7 Taylor exp of the binning rule, every operation
+ * rounded to nearest), is below min_opacity.  Each dead primitive draws a
+ * live source with probability proportional to opacity: weights
+ * floor(o 2^24), inclusive 64-bit prefix sums W, its random word r[i] picks
+ * t = floor(r[i] W_total / 2^32) and the source is the first j with W_j > t.
+ * Every parameter of the source is copied to it; a source with N copies in
+ * all (itself included) gets o' = 1 - (1 - o)^(1/N) on each; the copies'
+ * Adam moments are zeroed.  Nothing changes when no primitive is live.
+ *   planes [15 + 6M][pitch] in/out; adam_m, adam_v same layout, in/out, or NULL
+ *   rnd     [n] in: uniform 32-bit random words
+ *   ws      beta_relocate_workspace_bytes(n) bytes, 256-byte aligned
+ *   src_out [n] out or NULL: source index of each primitive, -1 if kept
+ *   d_count device int32 out: number of relocated primitives */
+size_t beta_relocate_workspace_bytes(int32_t n);
+int beta_relocate(int32_t n, int32_t pitch, int32_t n_lobes, float* planes, float* adam_m,
+                  float* adam_v, const uint32_t* rnd, float min_opacity, void* ws, size_t ws_bytes,
+                  int32_t* src_out, int32_t* d_count, beta_stream_t stream);
+
+/* ---- the composite loss with the DSSIM term (Sec. 3.4) -------------- */
+
+/* Per view v, colour x and target y (layout of beta_raster_fwd's colour):
+ *   loss[v] = (1 - lambda_ssim) mean|x - y| + lambda_ssim (1 - mean SSIM(x, y))
+ * with SSIM from Gaussian-weighted local statistics (11 taps, sigma 1.5,
+ * separable, zero outside the image, C1 = 0.01^2, C2 = 0.03^2, dynamic range
+ * 1), means over the view's 3 W H values; dL_dcolor = d(sum_v loss[v])/dx
+ * (sign(0) = 0 in the L1 part).  The appendix uses lambda_ssim = 0.2;
+ * lambda_ssim = 0 is the plain L1 loss of beta_l1_loss.
+ *   loss      device float[n_views] out;  dL_dcolor: layout of color, out
+ *   ws        beta_dssim_workspace_bytes() bytes, 256-byte aligned
+ * Returns BETA_ERR_ARG for null pointers or lambda_ssim outside [0, 1]. */
+size_t beta_dssim_workspace_bytes(const beta_camera* cams /* host */, int32_t n_views);
+int beta_l1_dssim_loss(const beta_camera* cams, int32_t n_views, const float* color,
+                       const float* target, float lambda_ssim, float* loss, float* dL_dcolor,
+                       void* ws, size_t ws_bytes, beta_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

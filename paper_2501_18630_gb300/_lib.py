@@ -30,7 +30,8 @@ EXPORTS = [
     "beta_total_tiles", "beta_total_pixels", "beta_binsort_workspace_bytes", "beta_grad2d_bytes",
     "beta_l1_workspace_bytes", "beta_project", "beta_bin_sort", "beta_raster_fwd", "beta_l1_loss",
     "beta_raster_bwd", "beta_project_bwd", "beta_bin_sort_static", "beta_schedule_bytes",
-    "beta_schedule",
+    "beta_schedule", "beta_adam_default_opts", "beta_adam_step", "beta_relocate_workspace_bytes",
+    "beta_relocate", "beta_dssim_workspace_bytes", "beta_l1_dssim_loss",
 ]
 
 
@@ -50,6 +51,16 @@ class BetaOpts(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("batch_s", ctypes.c_int32),
                 ("color_mode", ctypes.c_int32), ("t_eps", ctypes.c_float), ("alpha_max", ctypes.c_float),
                 ("blur_eps", ctypes.c_float), ("b_lo", ctypes.c_float), ("b_hi", ctypes.c_float)]
+
+
+class BetaAdamOpts(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 9), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("lambda_o", ctypes.c_float), ("lambda_sigma", ctypes.c_float),
+                ("lambda_eps", ctypes.c_float), ("noise_b", ctypes.c_float), ("step", ctypes.c_int32)]
+
+
+# learning-rate groups of BetaAdamOpts.lr, in order
+ADAM_GROUPS = ("mean", "log_scale", "quat", "opacity", "b", "c0", "lobe_dir", "lobe_b", "lobe_color")
 
 
 class BetaError(RuntimeError):
@@ -93,6 +104,13 @@ def load(path: str = LIB_PATH):
             "beta_schedule": (ctypes.c_int, [C, i32, O, vp, vp, vp, vp]),
             "beta_project_bwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp]),
             "beta_bin_sort_static": (ctypes.c_int, [P, C, i32, O, vp, vp, i64, vp, vp, vp, vp]),
+            "beta_adam_default_opts": (None, [ctypes.POINTER(BetaAdamOpts)]),
+            "beta_adam_step": (ctypes.c_int, [i32, i32, i32, vp, vp, vp, vp, vp,
+                                              ctypes.POINTER(BetaAdamOpts), vp, vp]),
+            "beta_relocate_workspace_bytes": (sz, [i32]),
+            "beta_dssim_workspace_bytes": (sz, [C, i32]),
+            "beta_l1_dssim_loss": (ctypes.c_int, [C, i32, vp, vp, ctypes.c_float, vp, vp, vp, sz, vp]),
+            "beta_relocate": (ctypes.c_int, [i32, i32, i32, vp, vp, vp, vp, ctypes.c_float, vp, sz, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -105,6 +123,17 @@ def load(path: str = LIB_PATH):
 def check(fn: str, code: int):
     if code != BETA_OK:
         raise BetaError(fn, code, load().beta_status_string(code).decode())
+
+
+def adam_default_opts(lr: dict | None = None, **kw) -> BetaAdamOpts:
+    """The appendix hyperparameters; lr maps ADAM_GROUPS names to rates."""
+    o = BetaAdamOpts()
+    load().beta_adam_default_opts(ctypes.byref(o))
+    for k, v in (lr or {}).items():
+        o.lr[ADAM_GROUPS.index(k)] = v
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
 
 
 def default_opts(**kw) -> BetaOpts:

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbetasplat.so")
-SOURCES = ["beta_api.cu", "beta_project.cu", "beta_sort.cu", "beta_raster.cu"]
+SOURCES = ["beta_api.cu", "beta_project.cu", "beta_sort.cu", "beta_raster.cu", "beta_optim.cu", "beta_ssim.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

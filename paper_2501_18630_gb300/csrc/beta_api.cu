@@ -327,4 +327,79 @@ int beta_project_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_
                                         (cudaStream_t)stream));
 }
 
+void beta_adam_default_opts(beta_adam_opts* o) {
+  if (!o) return;
+  const float lr[9] = {1.6e-4f, 5e-3f, 1e-3f, 5e-2f, 1e-3f, 2.5e-3f, 2.5e-3f, 2.5e-3f, 2.5e-3f};
+  for (int k = 0; k < 9; ++k) o->lr[k] = lr[k];
+  o->beta1 = 0.9f;
+  o->beta2 = 0.999f;
+  o->eps = 1e-15f;
+  o->lambda_o = 0.01f;
+  o->lambda_sigma = 0.01f;
+  o->lambda_eps = 5e4f;
+  o->noise_b = 3.2188758248682006f;   // ln 25
+  o->step = 1;
+}
+
+int beta_adam_step(int32_t n, int32_t pitch, int32_t n_lobes, float* planes, const float* grad,
+                   float* adam_m, float* adam_v, const float* eta, const beta_adam_opts* opt,
+                   double* reg_loss, beta_stream_t stream) {
+  if (!opt || n < 0 || pitch < n || pitch % 4 != 0 || n_lobes < 0 || n_lobes > BETA_MAX_LOBES)
+    return BETA_ERR_ARG;
+  if (!planes || !grad || !adam_m || !adam_v || !eta) return BETA_ERR_ARG;
+  if (!aligned16(planes) || !aligned16(grad) || !aligned16(adam_m) || !aligned16(adam_v) || !aligned16(eta))
+    return BETA_ERR_ARG;
+  if (opt->step < 1 || !(opt->beta1 >= 0.0f && opt->beta1 < 1.0f) || !(opt->beta2 >= 0.0f && opt->beta2 < 1.0f) ||
+      !(opt->eps > 0.0f) || !isfinite(opt->noise_b))
+    return BETA_ERR_ARG;
+  AdamDev a;
+  for (int k = 0; k < 9; ++k) a.lr[k] = opt->lr[k];
+  a.beta1 = opt->beta1;
+  a.beta2 = opt->beta2;
+  a.eps = opt->eps;
+  a.inv_c1 = (float)(1.0 / (1.0 - pow((double)opt->beta1, (double)opt->step)));
+  a.inv_c2 = (float)(1.0 / (1.0 - pow((double)opt->beta2, (double)opt->step)));
+  a.lambda_o = opt->lambda_o;
+  a.lambda_sigma = opt->lambda_sigma;
+  a.noise_scale = opt->lambda_eps * opt->lr[0];
+  a.noise_pow = (float)(4.0 * exp((double)opt->noise_b));
+  return cuda_status(launch_adam(n_lobes, planes, grad, adam_m, adam_v, eta, n, pitch, a, reg_loss,
+                                 (cudaStream_t)stream));
+}
+
+size_t beta_relocate_workspace_bytes(int32_t n) { return n > 0 ? reloc_ws_bytes(n) : 0; }
+
+int beta_relocate(int32_t n, int32_t pitch, int32_t n_lobes, float* planes, float* adam_m,
+                  float* adam_v, const uint32_t* rnd, float min_opacity, void* ws, size_t ws_bytes,
+                  int32_t* src_out, int32_t* d_count, beta_stream_t stream) {
+  if (n < 0 || pitch < n || pitch % 4 != 0 || n_lobes < 0 || n_lobes > BETA_MAX_LOBES) return BETA_ERR_ARG;
+  if (!planes || !rnd || !d_count || !(min_opacity >= 0.0f && min_opacity <= 1.0f)) return BETA_ERR_ARG;
+  if (n > 0 && (!ws || ws_bytes < reloc_ws_bytes(n) || ((uintptr_t)ws & 255u) != 0)) return BETA_ERR_WORKSPACE;
+  return cuda_status(launch_relocate(n, pitch, 15 + 6 * n_lobes, planes, adam_m, adam_v, rnd, min_opacity,
+                                     ws, src_out, d_count, (cudaStream_t)stream));
+}
+
+size_t beta_dssim_workspace_bytes(const beta_camera* cams, int32_t n_views) {
+  beta_opts o;
+  beta_default_opts(&o);
+  ViewTable vt;
+  if (build_views(cams, n_views, &o, vt) != BETA_OK) return 0;
+  return ssim_ws_bytes(vt);
+}
+
+int beta_l1_dssim_loss(const beta_camera* cams, int32_t n_views, const float* color,
+                       const float* target, float lambda_ssim, float* loss, float* dL_dcolor,
+                       void* ws, size_t ws_bytes, beta_stream_t stream) {
+  if (!color || !target || !loss || !dL_dcolor || !(lambda_ssim >= 0.0f && lambda_ssim <= 1.0f))
+    return BETA_ERR_ARG;
+  beta_opts o;
+  beta_default_opts(&o);
+  ViewTable vt;
+  int e;
+  if ((e = build_views(cams, n_views, &o, vt)) != BETA_OK) return e;
+  if (!ws || ws_bytes < ssim_ws_bytes(vt) || ((uintptr_t)ws & 255u) != 0) return BETA_ERR_WORKSPACE;
+  return cuda_status(launch_ssim_loss(vt, color, target, lambda_ssim, loss, dL_dcolor, ws,
+                                      (cudaStream_t)stream));
+}
+
 }  // extern "C"

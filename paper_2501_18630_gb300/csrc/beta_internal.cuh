@@ -297,6 +297,31 @@ __device__ __forceinline__ float lg2_approx(float x) {
   return y;
 }
 
+// lobe count -> template instantiation (M = 0..8)
+#define BETA_DISPATCH_M(M_, CALL) \
+  switch (M_) {                   \
+    case 0: return CALL(0);       \
+    case 1: return CALL(1);       \
+    case 2: return CALL(2);       \
+    case 3: return CALL(3);       \
+    case 4: return CALL(4);       \
+    case 5: return CALL(5);       \
+    case 6: return CALL(6);       \
+    case 7: return CALL(7);       \
+    case 8: return CALL(8);       \
+    default: return cudaErrorInvalidValue; \
+  }
+
+// Optimiser-step constants (beta_optim.cu).
+struct AdamDev {
+  float lr[9];                 // mean, log-scale, quaternion, opacity, b, c0, lobe dir, lobe b, lobe colour
+  float beta1, beta2, eps;
+  float inv_c1, inv_c2;        // 1 / (1 - beta^t)
+  float lambda_o, lambda_sigma;
+  float noise_scale;           // lambda_eps * lr_mu
+  float noise_pow;             // 4 e^b'
+};
+
 // ---------------------------------------------------------------------------
 // host-side launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -320,6 +345,16 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
                             int64_t cap, uint32_t* ranges, int64_t* d_count, int32_t* d_status,
                             void* ws, cudaStream_t s);
 
+cudaError_t launch_adam(int n_lobes, float* planes, const float* grad, float* m, float* v,
+                        const float* eta, int n, int pitch, const AdamDev& a, double* reg,
+                        cudaStream_t s);
+size_t ssim_ws_bytes(const ViewTable& vt);
+cudaError_t launch_ssim_loss(const ViewTable& vt, const float* color, const float* target, float lambda,
+                             float* loss, float* dL_dcolor, void* ws, cudaStream_t s);
+size_t reloc_ws_bytes(int n);
+cudaError_t launch_relocate(int n, int pitch, int n_planes, float* planes, float* m, float* v,
+                            const uint32_t* rnd, float min_opacity, void* ws, int32_t* src_out,
+                            int32_t* d_count, cudaStream_t s);
 cudaError_t launch_raster_fwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                               const uint32_t* vals, const uint32_t* ranges, float* color,
                               float* T_final, uint32_t* n_contrib, const int32_t* status,

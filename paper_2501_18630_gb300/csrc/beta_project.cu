@@ -429,20 +429,6 @@ static cudaError_t launch_project_bwd_m(const float* planes, int n, int pitch, c
   return cudaGetLastError();
 }
 
-#define BETA_DISPATCH_M(M_, CALL) \
-  switch (M_) {                   \
-    case 0: return CALL(0);       \
-    case 1: return CALL(1);       \
-    case 2: return CALL(2);       \
-    case 3: return CALL(3);       \
-    case 4: return CALL(4);       \
-    case 5: return CALL(5);       \
-    case 6: return CALL(6);       \
-    case 7: return CALL(7);       \
-    case 8: return CALL(8);       \
-    default: return cudaErrorInvalidValue; \
-  }
-
 cudaError_t launch_project(const float* planes, int n, int pitch, int n_lobes, const ViewTable& vt,
                            const RenderOpts& ro, ProjBuffers pb, cudaStream_t s) {
 #define CALL_P(m) launch_project_m<m>(planes, n, pitch, vt, ro, pb, s)

@@ -1,0 +1,258 @@
+// beta_ssim.cu -- the image side of the composite loss with the DSSIM term
+// (Sec. 3.4 of arXiv 2501.18630; lambda_SSIM = 0.2 in the appendix):
+//
+//   loss_v = (1 - lambda) mean|x - y| + lambda (1 - mean SSIM(x, y))
+//
+// per view v (colour x, target y, means over its 3 H W values), SSIM from
+// Gaussian-weighted local statistics (11 taps, sigma 1.5, separable, zero
+// outside the image; C1 = 0.01^2, C2 = 0.03^2):
+//   mu = G * x,  sigma_x^2 = G * x^2 - mu_x^2,  sigma_xy = G * x y - mu_x mu_y,
+//   S = (2 mu_x mu_y + C1)(2 sigma_xy + C2) / ((mu_x^2 + mu_y^2 + C1)(sigma_x^2 + sigma_y^2 + C2)).
+// Its gradient: with A1, A2, B1, B2 the four factors of S and d = 1/(B1 B2),
+// S depends on x through (mu_x, G * x^2, G * x y):
+//   a = dS/dmu_x = 2 mu_y A2 d - 2 mu_x S / B1 + 2 mu_x S / B2 - 2 mu_y A1 d
+//   b = 2 dS/dG*x^2 = -2 S / B2,   c = dS/dG*xy = 2 A1 d
+//   dL/dx = (1 - lambda) sign(x - y) / N - lambda / N (G*a + x G*b + y G*c).
+//
+// k_ssim_stats: one CTA per 32 x 16 pixel tile of one channel: the tile and a
+//   5-pixel halo of x and y in shared memory, the horizontal pass of the five
+//   products, the vertical pass per pixel, then S, (a, b, c) to the workspace
+//   and the tile's sums of S and |x - y| to per-view accumulators.
+// k_ssim_grad:  the same tiling over (a, b, c): blur them and form dL/dx.
+// k_ssim_loss:  the per-view losses.
+// HBM traffic per channel-pixel: x, y read twice, (a, b, c) written and read
+// once, dL/dx written: 44 bytes.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "beta_internal.cuh"
+
+namespace beta {
+
+namespace {
+
+constexpr int kTX = 32, kTY = 16, kR = 5, kWin = 2 * kR + 1;
+constexpr int kHX = kTX + 2 * kR, kHY = kTY + 2 * kR;
+constexpr float kC1 = 1e-4f, kC2 = 9e-4f;
+
+// normalised Gaussian taps (sigma 1.5), computed by the host launcher and
+// passed by value (kernel parameter space)
+struct SsimWin {
+  float g[kWin];
+};
+
+// view of an SSIM block (the per-view first block rides in ViewDev::pad0) and
+// the channel and tile of the block inside the view
+struct SsimBlock {
+  int v, ch, x0, y0, W, H;
+};
+
+__device__ __forceinline__ SsimBlock ssim_block(const ViewTable& vt, int b) {
+  int lo = 0, hi = vt.n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (vt.v[mid].pad0 <= b) lo = mid; else hi = mid - 1;
+  }
+  SsimBlock r;
+  r.v = lo;
+  r.W = vt.v[lo].width;
+  r.H = vt.v[lo].height;
+  const int ntx = (r.W + kTX - 1) / kTX, nty = (r.H + kTY - 1) / kTY;
+  int k = b - vt.v[lo].pad0;
+  r.ch = k / (ntx * nty);
+  k -= r.ch * ntx * nty;
+  r.y0 = (k / ntx) * kTY;
+  r.x0 = (k % ntx) * kTX;
+  return r;
+}
+
+__device__ __forceinline__ double block_sum_d(double x, double* s_w) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = x;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_w[w];
+  return t;
+}
+
+__global__ void __launch_bounds__(256) k_ssim_stats(ViewTable vt, SsimWin win, const float* __restrict__ color,
+                                                    const float* __restrict__ target,
+                                                    float* __restrict__ abc, int64_t plane,
+                                                    double* __restrict__ acc) {
+  __shared__ float s_x[kHY][kHX], s_y[kHY][kHX];
+  __shared__ float s_h[5][kHY][kTX];
+  __shared__ double s_w[8];
+  const SsimBlock B = ssim_block(vt, blockIdx.x);
+  const int64_t HW = (int64_t)B.W * B.H;
+  const int64_t base = 3 * vt.v[B.v].pix_off + B.ch * HW;
+  const float* xs = color + base;
+  const float* ys = target + base;
+  for (int k = threadIdx.x; k < kHY * kHX; k += blockDim.x) {
+    const int r = k / kHX, c = k - r * kHX;
+    const int gy = B.y0 - kR + r, gx = B.x0 - kR + c;
+    const bool in = gx >= 0 && gx < B.W && gy >= 0 && gy < B.H;
+    s_x[r][c] = in ? xs[(int64_t)gy * B.W + gx] : 0.0f;
+    s_y[r][c] = in ? ys[(int64_t)gy * B.W + gx] : 0.0f;
+  }
+  __syncthreads();
+  // horizontal pass of x, y, x^2, y^2, x y
+  for (int k = threadIdx.x; k < kHY * kTX; k += blockDim.x) {
+    const int r = k / kTX, c = k - r * kTX;
+    float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f;
+#pragma unroll
+    for (int t = 0; t < kWin; ++t) {
+      const float g = win.g[t], xv = s_x[r][c + t], yv = s_y[r][c + t];
+      h0 = fmaf(g, xv, h0);
+      h1 = fmaf(g, yv, h1);
+      h2 = fmaf(g, xv * xv, h2);
+      h3 = fmaf(g, yv * yv, h3);
+      h4 = fmaf(g, xv * yv, h4);
+    }
+    s_h[0][r][c] = h0;
+    s_h[1][r][c] = h1;
+    s_h[2][r][c] = h2;
+    s_h[3][r][c] = h3;
+    s_h[4][r][c] = h4;
+  }
+  __syncthreads();
+  double sum_s = 0.0, sum_l1 = 0.0;
+  for (int k = threadIdx.x; k < kTY * kTX; k += blockDim.x) {
+    const int r = k / kTX, c = k - r * kTX;
+    const int gy = B.y0 + r, gx = B.x0 + c;
+    if (gx >= B.W || gy >= B.H) continue;
+    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < kWin; ++t) {
+      const float g = win.g[t];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) m[q] = fmaf(g, s_h[q][r + t][c], m[q]);
+    }
+    const float mx = m[0], my = m[1];
+    const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
+    const float A1 = 2.0f * mx * my + kC1, A2 = 2.0f * sxy + kC2;
+    const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
+    const float d = 1.0f / (B1 * B2);
+    const float S = A1 * A2 * d;
+    const float a = 2.0f * my * A2 * d - 2.0f * mx * S / B1 + 2.0f * mx * S / B2 - 2.0f * my * A1 * d;
+    const int64_t at = base + (int64_t)gy * B.W + gx;
+    abc[at] = a;
+    abc[plane + at] = -2.0f * S / B2;
+    abc[2 * plane + at] = 2.0f * A1 * d;
+    sum_s += S;
+    sum_l1 += fabsf(s_x[r + kR][c + kR] - s_y[r + kR][c + kR]);
+  }
+  const double ts = block_sum_d(sum_s, s_w);
+  __syncthreads();
+  const double tl = block_sum_d(sum_l1, s_w);
+  if (threadIdx.x == 0) {
+    atomicAdd(&acc[2 * B.v], ts);
+    atomicAdd(&acc[2 * B.v + 1], tl);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ssim_grad(ViewTable vt, SsimWin win, const float* __restrict__ color,
+                                                   const float* __restrict__ target,
+                                                   const float* __restrict__ abc, int64_t plane, float lambda,
+                                                   float* __restrict__ dLdC) {
+  __shared__ float s_m[3][kHY][kHX];
+  __shared__ float s_h[3][kHY][kTX];
+  const SsimBlock B = ssim_block(vt, blockIdx.x);
+  const int64_t HW = (int64_t)B.W * B.H;
+  const int64_t base = 3 * vt.v[B.v].pix_off + B.ch * HW;
+  for (int k = threadIdx.x; k < kHY * kHX; k += blockDim.x) {
+    const int r = k / kHX, c = k - r * kHX;
+    const int gy = B.y0 - kR + r, gx = B.x0 - kR + c;
+    const bool in = gx >= 0 && gx < B.W && gy >= 0 && gy < B.H;
+    const int64_t at = base + (int64_t)gy * B.W + gx;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s_m[q][r][c] = in ? abc[q * plane + at] : 0.0f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kHY * kTX; k += blockDim.x) {
+    const int r = k / kTX, c = k - r * kTX;
+    float h[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < kWin; ++t) {
+      const float g = win.g[t];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) h[q] = fmaf(g, s_m[q][r][c + t], h[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s_h[q][r][c] = h[q];
+  }
+  __syncthreads();
+  const float inv_n = 1.0f / (3.0f * (float)HW);
+  for (int k = threadIdx.x; k < kTY * kTX; k += blockDim.x) {
+    const int r = k / kTX, c = k - r * kTX;
+    const int gy = B.y0 + r, gx = B.x0 + c;
+    if (gx >= B.W || gy >= B.H) continue;
+    float gm[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < kWin; ++t) {
+      const float g = win.g[t];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) gm[q] = fmaf(g, s_h[q][r + t][c], gm[q]);
+    }
+    const int64_t at = base + (int64_t)gy * B.W + gx;
+    const float xv = color[at], yv = target[at];
+    const float dif = xv - yv;
+    const float sgn = dif > 0.0f ? 1.0f : (dif < 0.0f ? -1.0f : 0.0f);
+    const float dS = gm[0] + xv * gm[1] + yv * gm[2];
+    dLdC[at] = inv_n * ((1.0f - lambda) * sgn - lambda * dS);
+  }
+}
+
+__global__ void k_ssim_loss(ViewTable vt, const double* __restrict__ acc, float lambda, float* __restrict__ loss) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= vt.n_views) return;
+  const double n = 3.0 * (double)vt.v[v].width * vt.v[v].height;
+  loss[v] = (float)((1.0 - lambda) * acc[2 * v + 1] / n + lambda * (1.0 - acc[2 * v] / n));
+}
+
+int ssim_blocks(ViewTable& vt) {
+  int b = 0;
+  for (int v = 0; v < vt.n_views; ++v) {
+    vt.v[v].pad0 = b;
+    const int ntx = (vt.v[v].width + kTX - 1) / kTX, nty = (vt.v[v].height + kTY - 1) / kTY;
+    b += 3 * ntx * nty;
+  }
+  return b;
+}
+
+}  // namespace
+
+size_t ssim_ws_bytes(const ViewTable& vt) {
+  // (a, b, c) planes over every view's pixels and channels, then the per-view sums
+  return ((size_t)9 * vt.total_pixels * sizeof(float) + 255) / 256 * 256 + (size_t)2 * vt.n_views * sizeof(double);
+}
+
+cudaError_t launch_ssim_loss(const ViewTable& vt_in, const float* color, const float* target, float lambda,
+                             float* loss, float* dL_dcolor, void* ws, cudaStream_t s) {
+  SsimWin win;
+  {
+    double sum = 0.0, gd[kWin];
+    for (int t = 0; t < kWin; ++t) {
+      const double k = t - kR;
+      gd[t] = exp(-k * k / (2.0 * 1.5 * 1.5));
+      sum += gd[t];
+    }
+    for (int t = 0; t < kWin; ++t) win.g[t] = (float)(gd[t] / sum);
+  }
+  ViewTable vt = vt_in;
+  const int nb = ssim_blocks(vt);
+  if (nb <= 0) return cudaSuccess;
+  const int64_t plane = 3 * vt.total_pixels;
+  float* abc = (float*)ws;
+  double* acc = (double*)((char*)ws + ((size_t)9 * vt.total_pixels * sizeof(float) + 255) / 256 * 256);
+  cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)2 * vt.n_views * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  k_ssim_stats<<<nb, 256, 0, s>>>(vt, win, color, target, abc, plane, acc);
+  k_ssim_grad<<<nb, 256, 0, s>>>(vt, win, color, target, abc, plane, lambda, dL_dcolor);
+  k_ssim_loss<<<(vt.n_views + 63) / 64, 64, 0, s>>>(vt, acc, lambda, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace beta

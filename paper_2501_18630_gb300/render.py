@@ -123,6 +123,17 @@ class Rasterizer:
             _vp(self.l1_ws), self.l1_ws.numel(), _stream()))
         return self.loss, self.dL_dcolor
 
+    def dssim_loss(self, target: torch.Tensor, lambda_ssim: float = 0.2):
+        """(1 - lambda) L1 + lambda (1 - SSIM) per view and its gradient (Sec. 3.4)."""
+        assert target.numel() == self.color.numel() and target.is_contiguous()
+        if getattr(self, "ssim_ws", None) is None:
+            nb = int(self.L.beta_dssim_workspace_bytes(self.cams, self.V))
+            self.ssim_ws = torch.empty(max(nb, 1), dtype=torch.uint8, device=self.color.device)
+        _lib.check("beta_l1_dssim_loss", self.L.beta_l1_dssim_loss(
+            self.cams, self.V, _vp(self.color), _vp(target), ctypes.c_float(lambda_ssim), _vp(self.loss),
+            _vp(self.dL_dcolor), _vp(self.ssim_ws), self.ssim_ws.numel(), _stream()))
+        return self.loss, self.dL_dcolor
+
     def raster_bwd(self, planes, dL_dcolor):
         prm = self.params(planes)
         assert dL_dcolor.numel() == self.color.numel() and dL_dcolor.is_contiguous()

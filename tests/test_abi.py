@@ -43,6 +43,16 @@ def test_header_prototypes_match_binding(L):
         assert getattr(L, name).argtypes is not None or name in ("beta_version",), name
 
 
+def test_adam_defaults_are_the_papers(L):
+    ao = _lib.adam_default_opts()
+    lr = dict(zip(_lib.ADAM_GROUPS, list(ao.lr)))
+    assert lr["mean"] == pytest.approx(1.6e-4) and lr["opacity"] == pytest.approx(0.05)
+    assert lr["log_scale"] == pytest.approx(5e-3) and lr["quat"] == pytest.approx(1e-3)
+    assert lr["b"] == pytest.approx(1e-3) and lr["c0"] == pytest.approx(2.5e-3)
+    assert ao.lambda_o == pytest.approx(0.01) and ao.lambda_sigma == pytest.approx(0.01)
+    assert ao.lambda_eps == pytest.approx(5e4) and ao.noise_b == pytest.approx(math.log(25.0))
+
+
 def test_host_queries(L):
     o = _lib.default_opts()
     assert (o.tile_w, o.tile_h, o.batch_s, o.color_mode) == (16, 16, 256, 0)
@@ -86,6 +96,12 @@ def test_argument_errors_are_returned_without_launch(L):
     # capacity beyond 2^31 - 1
     r = L.beta_bin_sort(ctypes.byref(prm), cams, 1, ctypes.byref(o), vp, vp, 1 << 31, vp, vp, vp, vp, 1 << 40, None)
     assert r == _lib.BETA_ERR_ARG
+    # optimiser step: null pointers, n > pitch, step < 1
+    ao = _lib.adam_default_opts()
+    assert L.beta_adam_step(10, 32, 1, None, vp, vp, vp, vp, ctypes.byref(ao), None, None) == _lib.BETA_ERR_ARG
+    assert L.beta_adam_step(40, 32, 1, vp, vp, vp, vp, vp, ctypes.byref(ao), None, None) == _lib.BETA_ERR_ARG
+    ao.step = 0
+    assert L.beta_adam_step(10, 32, 1, vp, vp, vp, vp, vp, ctypes.byref(ao), None, None) == _lib.BETA_ERR_ARG
     # invalid alpha_max
     o3 = _lib.default_opts(alpha_max=1.0)
     assert L.beta_project(ctypes.byref(prm), cams, 1, ctypes.byref(o3), vp, None) == _lib.BETA_ERR_ARG
