@@ -456,7 +456,21 @@ def main():
             "what": "beta_adam_step: Adam + regulariser gradients + Beta-scaled position noise on all raw "
                     "parameters (reads params, grads, 2 moments, noise; writes params, 2 moments); L2 flushed "
                     "before each timed launch"}
-        del opt_planes, adam, flush
+        # relocation of dead primitives (the scene's opacity logits, threshold 0.005)
+        n_dead = 0
+        for _ in range(2):
+            reloc_planes = planes.clone()
+            radam = BetaAdam(reloc_planes, sc.n, sc.n_lobes)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            cnt, _ = radam.relocate(reloc_planes, 0.005)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            n_dead = int(cnt.item())
+        extras["relocation"] = {"ms": e0.elapsed_time(e1), "n_betas": sc.n, "relocated": n_dead,
+                                "what": "beta_relocate: fixed-rule opacities, 64-bit cumulative weights, one "
+                                        "binary search per dead primitive, opacity-only update, copies"}
+        del opt_planes, adam, flush, reloc_planes, radam
 
         # ---- the composite loss with the DSSIM term (Sec. 3.4), HBM-bound ---
         for _ in range(args.warmup):

@@ -14,12 +14,15 @@
 //   b = 2 dS/dG*x^2 = -2 S / B2,   c = dS/dG*xy = 2 A1 d
 //   dL/dx = (1 - lambda) sign(x - y) / N - lambda / N (G*a + x G*b + y G*c).
 //
-// k_ssim_stats: one CTA per 32 x 16 pixel tile of one channel: the tile and a
-//   5-pixel halo of x and y in shared memory, the horizontal pass of the five
-//   products, the vertical pass per pixel, then S, (a, b, c) to the workspace
-//   and the tile's sums of S and |x - y| to per-view accumulators.
+// k_ssim_stats: one CTA per 32 x 32 pixel tile of one channel: x and y over
+//   the tile and a 5-pixel halo in shared memory, the
+//   horizontal and vertical 11-tap passes with each thread sliding a register
+//   window over 4 outputs (one shared-memory load per input instead of one per
+//   tap), then S, (a, b, c) to the workspace and the tile's sums of S and
+//   |x - y| as per-block partials.
 // k_ssim_grad:  the same tiling over (a, b, c): blur them and form dL/dx.
-// k_ssim_loss:  the per-view losses.
+// k_ssim_loss:  per view, the sum of its blocks' partials (fixed order: the
+//   loss is deterministic) and the loss.
 // HBM traffic per channel-pixel: x, y read twice, (a, b, c) written and read
 // once, dL/dx written: 44 bytes.
 #include <cuda_runtime.h>
@@ -32,8 +35,16 @@ namespace beta {
 
 namespace {
 
-constexpr int kTX = 32, kTY = 16, kR = 5, kWin = 2 * kR + 1;
+constexpr int kTX = 32, kTY = 32, kR = 5, kWin = 2 * kR + 1;
+constexpr int kRun = 4;   // outputs per thread in each filter pass (sliding register window)
 constexpr int kHX = kTX + 2 * kR, kHY = kTY + 2 * kR;
+// row stride of the staged halo tiles: 45 = 1 (mod 4), so the four rows a
+// warp reads in the horizontal pass (8 lanes each, 4 columns apart) fall in
+// distinct banks
+constexpr int kSX = 45;
+// row stride of the horizontal-pass results: 33, so the same pass's stores
+// (rows apart by one, 4 columns apart) fall in distinct banks
+constexpr int kSH = kTX + 1;
 constexpr float kC1 = 1e-4f, kC2 = 9e-4f;
 
 // normalised Gaussian taps (sigma 1.5), computed by the host launcher and
@@ -78,12 +89,48 @@ __device__ __forceinline__ double block_sum_d(double x, double* s_w) {
   return t;
 }
 
+// Horizontal pass over a staged (kHY x kHX) tile: row r, columns c0 .. c0 +
+// kRun - 1 of the output, from a register window of kRun + 2 kR inputs.
+// PRODUCTS: the sources are x and y, and the five filtered quantities are
+// x, y, x^2, y^2, x y (formed in registers).
+template <int Q, bool PRODUCTS>
+__device__ __forceinline__ void hpass_run(const float (*src)[kHY][kSX], const SsimWin& win, int r, int c0,
+                                          float (&out)[Q][kRun]) {
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) out[q][j] = 0.0f;
+#pragma unroll
+  for (int t = 0; t < kRun + 2 * kR; ++t) {
+    float v[Q];
+    if (PRODUCTS) {
+      const float xv = src[0][r][c0 + t], yv = src[1][r][c0 + t];
+      v[0] = xv;
+      v[1] = yv;
+      v[2] = xv * xv;
+      v[3] = yv * yv;
+      v[4] = xv * yv;
+    } else {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) v[q] = src[q][r][c0 + t];
+    }
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+      const int k = t - j;                 // tap of input t for output j
+      if (k >= 0 && k < kWin) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) out[q][j] = fmaf(win.g[k], v[q], out[q][j]);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_ssim_stats(ViewTable vt, SsimWin win, const float* __restrict__ color,
                                                     const float* __restrict__ target,
                                                     float* __restrict__ abc, int64_t plane,
                                                     double* __restrict__ acc) {
-  __shared__ float s_x[kHY][kHX], s_y[kHY][kHX];
-  __shared__ float s_h[5][kHY][kTX];
+  __shared__ float s_in[2][kHY][kSX];     // x, y over the tile and its halo
+  __shared__ float s_h[5][kHY][kSH];      // their horizontal pass
   __shared__ double s_w[8];
   const SsimBlock B = ssim_block(vt, blockIdx.x);
   const int64_t HW = (int64_t)B.W * B.H;
@@ -94,62 +141,72 @@ __global__ void __launch_bounds__(256) k_ssim_stats(ViewTable vt, SsimWin win, c
     const int r = k / kHX, c = k - r * kHX;
     const int gy = B.y0 - kR + r, gx = B.x0 - kR + c;
     const bool in = gx >= 0 && gx < B.W && gy >= 0 && gy < B.H;
-    s_x[r][c] = in ? xs[(int64_t)gy * B.W + gx] : 0.0f;
-    s_y[r][c] = in ? ys[(int64_t)gy * B.W + gx] : 0.0f;
+    const float xv = in ? xs[(int64_t)gy * B.W + gx] : 0.0f;
+    const float yv = in ? ys[(int64_t)gy * B.W + gx] : 0.0f;
+    s_in[0][r][c] = xv;
+    s_in[1][r][c] = yv;
   }
   __syncthreads();
-  // horizontal pass of x, y, x^2, y^2, x y
-  for (int k = threadIdx.x; k < kHY * kTX; k += blockDim.x) {
-    const int r = k / kTX, c = k - r * kTX;
-    float h0 = 0.f, h1 = 0.f, h2 = 0.f, h3 = 0.f, h4 = 0.f;
+  for (int k = threadIdx.x; k < kHY * (kTX / kRun); k += blockDim.x) {
+    const int r = k / (kTX / kRun), c0 = (k - r * (kTX / kRun)) * kRun;
+    float h[5][kRun];
+    hpass_run<5, true>(s_in, win, r, c0, h);
 #pragma unroll
-    for (int t = 0; t < kWin; ++t) {
-      const float g = win.g[t], xv = s_x[r][c + t], yv = s_y[r][c + t];
-      h0 = fmaf(g, xv, h0);
-      h1 = fmaf(g, yv, h1);
-      h2 = fmaf(g, xv * xv, h2);
-      h3 = fmaf(g, yv * yv, h3);
-      h4 = fmaf(g, xv * yv, h4);
-    }
-    s_h[0][r][c] = h0;
-    s_h[1][r][c] = h1;
-    s_h[2][r][c] = h2;
-    s_h[3][r][c] = h3;
-    s_h[4][r][c] = h4;
+    for (int q = 0; q < 5; ++q)
+#pragma unroll
+      for (int j = 0; j < kRun; ++j) s_h[q][r][c0 + j] = h[q][j];
   }
   __syncthreads();
+  // vertical pass: column c, rows r0 .. r0 + kRun - 1 from a register window
   double sum_s = 0.0, sum_l1 = 0.0;
-  for (int k = threadIdx.x; k < kTY * kTX; k += blockDim.x) {
-    const int r = k / kTX, c = k - r * kTX;
-    const int gy = B.y0 + r, gx = B.x0 + c;
-    if (gx >= B.W || gy >= B.H) continue;
-    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  {
+    const int c = threadIdx.x % kTX, r0 = (threadIdx.x / kTX) * kRun;
+    float m[5][kRun];
 #pragma unroll
-    for (int t = 0; t < kWin; ++t) {
-      const float g = win.g[t];
+    for (int q = 0; q < 5; ++q)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) m[q] = fmaf(g, s_h[q][r + t][c], m[q]);
+      for (int j = 0; j < kRun; ++j) m[q][j] = 0.0f;
+#pragma unroll
+    for (int t = 0; t < kRun + 2 * kR; ++t) {
+      float v[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) v[q] = s_h[q][r0 + t][c];
+#pragma unroll
+      for (int j = 0; j < kRun; ++j) {
+        const int k = t - j;
+        if (k >= 0 && k < kWin) {
+#pragma unroll
+          for (int q = 0; q < 5; ++q) m[q][j] = fmaf(win.g[k], v[q], m[q][j]);
+        }
+      }
     }
-    const float mx = m[0], my = m[1];
-    const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-    const float A1 = 2.0f * mx * my + kC1, A2 = 2.0f * sxy + kC2;
-    const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-    const float d = 1.0f / (B1 * B2);
-    const float S = A1 * A2 * d;
-    const float a = 2.0f * my * A2 * d - 2.0f * mx * S / B1 + 2.0f * mx * S / B2 - 2.0f * my * A1 * d;
-    const int64_t at = base + (int64_t)gy * B.W + gx;
-    abc[at] = a;
-    abc[plane + at] = -2.0f * S / B2;
-    abc[2 * plane + at] = 2.0f * A1 * d;
-    sum_s += S;
-    sum_l1 += fabsf(s_x[r + kR][c + kR] - s_y[r + kR][c + kR]);
+    const int gx = B.x0 + c;
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+      const int gy = B.y0 + r0 + j;
+      if (gx >= B.W || gy >= B.H) continue;
+      const float mx = m[0][j], my = m[1][j];
+      const float sxx = m[2][j] - mx * mx, syy = m[3][j] - my * my, sxy = m[4][j] - mx * my;
+      const float A1 = 2.0f * mx * my + kC1, A2 = 2.0f * sxy + kC2;
+      const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
+      const float iB1 = __frcp_rn(B1), iB2 = __frcp_rn(B2);
+      const float d = iB1 * iB2;
+      const float S = A1 * A2 * d;
+      const float a = 2.0f * my * A2 * d - 2.0f * mx * S * iB1 + 2.0f * mx * S * iB2 - 2.0f * my * A1 * d;
+      const int64_t at = base + (int64_t)gy * B.W + gx;
+      abc[at] = a;
+      abc[plane + at] = -2.0f * S * iB2;
+      abc[2 * plane + at] = 2.0f * A1 * d;
+      sum_s += S;
+      sum_l1 += fabsf(s_in[0][r0 + j + kR][c + kR] - s_in[1][r0 + j + kR][c + kR]);
+    }
   }
   const double ts = block_sum_d(sum_s, s_w);
   __syncthreads();
   const double tl = block_sum_d(sum_l1, s_w);
-  if (threadIdx.x == 0) {
-    atomicAdd(&acc[2 * B.v], ts);
-    atomicAdd(&acc[2 * B.v + 1], tl);
+  if (threadIdx.x == 0) {   // per-block partial sums, reduced per view by k_ssim_loss
+    acc[2 * blockIdx.x] = ts;
+    acc[2 * blockIdx.x + 1] = tl;
   }
 }
 
@@ -157,8 +214,8 @@ __global__ void __launch_bounds__(256) k_ssim_grad(ViewTable vt, SsimWin win, co
                                                    const float* __restrict__ target,
                                                    const float* __restrict__ abc, int64_t plane, float lambda,
                                                    float* __restrict__ dLdC) {
-  __shared__ float s_m[3][kHY][kHX];
-  __shared__ float s_h[3][kHY][kTX];
+  __shared__ float s_m[3][kHY][kSX];
+  __shared__ float s_h[3][kHY][kSH];
   const SsimBlock B = ssim_block(vt, blockIdx.x);
   const int64_t HW = (int64_t)B.W * B.H;
   const int64_t base = 3 * vt.v[B.v].pix_off + B.ch * HW;
@@ -171,45 +228,69 @@ __global__ void __launch_bounds__(256) k_ssim_grad(ViewTable vt, SsimWin win, co
     for (int q = 0; q < 3; ++q) s_m[q][r][c] = in ? abc[q * plane + at] : 0.0f;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < kHY * kTX; k += blockDim.x) {
-    const int r = k / kTX, c = k - r * kTX;
-    float h[3] = {0.f, 0.f, 0.f};
+  for (int k = threadIdx.x; k < kHY * (kTX / kRun); k += blockDim.x) {
+    const int r = k / (kTX / kRun), c0 = (k - r * (kTX / kRun)) * kRun;
+    float h[3][kRun];
+    hpass_run<3, false>(s_m, win, r, c0, h);
 #pragma unroll
-    for (int t = 0; t < kWin; ++t) {
-      const float g = win.g[t];
+    for (int q = 0; q < 3; ++q)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) h[q] = fmaf(g, s_m[q][r][c + t], h[q]);
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) s_h[q][r][c] = h[q];
+      for (int j = 0; j < kRun; ++j) s_h[q][r][c0 + j] = h[q][j];
   }
   __syncthreads();
   const float inv_n = 1.0f / (3.0f * (float)HW);
-  for (int k = threadIdx.x; k < kTY * kTX; k += blockDim.x) {
-    const int r = k / kTX, c = k - r * kTX;
-    const int gy = B.y0 + r, gx = B.x0 + c;
-    if (gx >= B.W || gy >= B.H) continue;
-    float gm[3] = {0.f, 0.f, 0.f};
+  const int c = threadIdx.x % kTX, r0 = (threadIdx.x / kTX) * kRun;
+  float m[3][kRun];
 #pragma unroll
-    for (int t = 0; t < kWin; ++t) {
-      const float g = win.g[t];
+  for (int q = 0; q < 3; ++q)
 #pragma unroll
-      for (int q = 0; q < 3; ++q) gm[q] = fmaf(g, s_h[q][r + t][c], gm[q]);
+    for (int j = 0; j < kRun; ++j) m[q][j] = 0.0f;
+#pragma unroll
+  for (int t = 0; t < kRun + 2 * kR; ++t) {
+    float v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) v[q] = s_h[q][r0 + t][c];
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+      const int k = t - j;
+      if (k >= 0 && k < kWin) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) m[q][j] = fmaf(win.g[k], v[q], m[q][j]);
+      }
     }
+  }
+  const int gx = B.x0 + c;
+#pragma unroll
+  for (int j = 0; j < kRun; ++j) {
+    const int gy = B.y0 + r0 + j;
+    if (gx >= B.W || gy >= B.H) continue;
     const int64_t at = base + (int64_t)gy * B.W + gx;
     const float xv = color[at], yv = target[at];
     const float dif = xv - yv;
     const float sgn = dif > 0.0f ? 1.0f : (dif < 0.0f ? -1.0f : 0.0f);
-    const float dS = gm[0] + xv * gm[1] + yv * gm[2];
+    const float dS = m[0][j] + xv * m[1][j] + yv * m[2][j];
     dLdC[at] = inv_n * ((1.0f - lambda) * sgn - lambda * dS);
   }
 }
 
-__global__ void k_ssim_loss(ViewTable vt, const double* __restrict__ acc, float lambda, float* __restrict__ loss) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= vt.n_views) return;
-  const double n = 3.0 * (double)vt.v[v].width * vt.v[v].height;
-  loss[v] = (float)((1.0 - lambda) * acc[2 * v + 1] / n + lambda * (1.0 - acc[2 * v] / n));
+// per view: the sums of its blocks' partials (fixed order), then the loss
+__global__ void __launch_bounds__(256) k_ssim_loss(ViewTable vt, const double* __restrict__ acc, int nb,
+                                                   float lambda, float* __restrict__ loss) {
+  __shared__ double s_w[8];
+  const int v = blockIdx.x;
+  const int b0 = vt.v[v].pad0, b1 = v + 1 < vt.n_views ? vt.v[v + 1].pad0 : nb;
+  double ss = 0.0, sl = 0.0;
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+    ss += acc[2 * b];
+    sl += acc[2 * b + 1];
+  }
+  const double ts = block_sum_d(ss, s_w);
+  __syncthreads();
+  const double tl = block_sum_d(sl, s_w);
+  if (threadIdx.x == 0) {
+    const double n = 3.0 * (double)vt.v[v].width * vt.v[v].height;
+    loss[v] = (float)((1.0 - lambda) * tl / n + lambda * (1.0 - ts / n));
+  }
 }
 
 int ssim_blocks(ViewTable& vt) {
@@ -225,8 +306,9 @@ int ssim_blocks(ViewTable& vt) {
 }  // namespace
 
 size_t ssim_ws_bytes(const ViewTable& vt) {
-  // (a, b, c) planes over every view's pixels and channels, then the per-view sums
-  return ((size_t)9 * vt.total_pixels * sizeof(float) + 255) / 256 * 256 + (size_t)2 * vt.n_views * sizeof(double);
+  // (a, b, c) planes over every view's pixels and channels, then two partial sums per block
+  ViewTable t = vt;
+  return ((size_t)9 * vt.total_pixels * sizeof(float) + 255) / 256 * 256 + (size_t)2 * ssim_blocks(t) * sizeof(double);
 }
 
 cudaError_t launch_ssim_loss(const ViewTable& vt_in, const float* color, const float* target, float lambda,
@@ -247,11 +329,9 @@ cudaError_t launch_ssim_loss(const ViewTable& vt_in, const float* color, const f
   const int64_t plane = 3 * vt.total_pixels;
   float* abc = (float*)ws;
   double* acc = (double*)((char*)ws + ((size_t)9 * vt.total_pixels * sizeof(float) + 255) / 256 * 256);
-  cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)2 * vt.n_views * sizeof(double), s);
-  if (e != cudaSuccess) return e;
   k_ssim_stats<<<nb, 256, 0, s>>>(vt, win, color, target, abc, plane, acc);
   k_ssim_grad<<<nb, 256, 0, s>>>(vt, win, color, target, abc, plane, lambda, dL_dcolor);
-  k_ssim_loss<<<(vt.n_views + 63) / 64, 64, 0, s>>>(vt, acc, lambda, loss);
+  k_ssim_loss<<<vt.n_views, 256, 0, s>>>(vt, acc, nb, lambda, loss);
   return cudaGetLastError();
 }
 
