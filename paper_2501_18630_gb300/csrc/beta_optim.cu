@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ planes, const 
   constexpr int NP = 15 + 6 * M;
   __shared__ double s_red[2][8];
   const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  double r_o = 0.0, r_s = 0.0;
+  // regulariser sums in fp32 within a warp, FP64 across the warps
+  float f_o = 0.0f, f_s = 0.0f;
   if (i0 < n) {
     const int cnt = min(4, n - i0);
     PrimPre pre[4];
@@ -115,8 +116,8 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ planes, const 
     for (int l = 0; l < 4; ++l)
       if (l < cnt) {
         pre[l] = prim_pre(planes, eta, pitch, i0 + l, a);
-        r_o += (double)a.lambda_o * pre[l].o;
-        r_s += (double)a.lambda_sigma * ((double)pre[l].s[0] + pre[l].s[1] + pre[l].s[2]);
+        f_o += a.lambda_o * pre[l].o;
+        f_s += a.lambda_sigma * (pre[l].s[0] + pre[l].s[1] + pre[l].s[2]);
       }
     if (cnt == 4) {
 #pragma unroll 2
@@ -165,13 +166,13 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ planes, const 
   if (reg) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      r_o += __shfl_xor_sync(0xffffffffu, r_o, off);
-      r_s += __shfl_xor_sync(0xffffffffu, r_s, off);
+      f_o += __shfl_xor_sync(0xffffffffu, f_o, off);
+      f_s += __shfl_xor_sync(0xffffffffu, f_s, off);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-      s_red[0][warp] = r_o;
-      s_red[1][warp] = r_s;
+      s_red[0][warp] = f_o;
+      s_red[1][warp] = f_s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -78,10 +78,12 @@ __device__ __forceinline__ SsimBlock ssim_block(const ViewTable& vt, int b) {
   return r;
 }
 
-__device__ __forceinline__ double block_sum_d(double x, double* s_w) {
+// Block sum (valid in thread 0): warp sums in fp32, the warps' sums in FP64
+// (GB300's FP64 pipe is narrow: no per-thread FP64 arithmetic).
+__device__ __forceinline__ double block_sum_d(float x, double* s_w) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = x;
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = (double)x;
   __syncthreads();
   double t = 0.0;
   if (threadIdx.x == 0)
@@ -137,14 +139,27 @@ __global__ void __launch_bounds__(256) k_ssim_stats(ViewTable vt, SsimWin win, c
   const int64_t base = 3 * vt.v[B.v].pix_off + B.ch * HW;
   const float* xs = color + base;
   const float* ys = target + base;
-  for (int k = threadIdx.x; k < kHY * kHX; k += blockDim.x) {
-    const int r = k / kHX, c = k - r * kHX;
-    const int gy = B.y0 - kR + r, gx = B.x0 - kR + c;
-    const bool in = gx >= 0 && gx < B.W && gy >= 0 && gy < B.H;
-    const float xv = in ? xs[(int64_t)gy * B.W + gx] : 0.0f;
-    const float yv = in ? ys[(int64_t)gy * B.W + gx] : 0.0f;
-    s_in[0][r][c] = xv;
-    s_in[1][r][c] = yv;
+  {
+    constexpr int kLd = (kHY * kHX + 255) / 256;
+    float lx[kLd], ly[kLd];
+#pragma unroll
+    for (int i = 0; i < kLd; ++i) {
+      const int k = threadIdx.x + i * 256;
+      const int r = k / kHX, c = k - r * kHX;
+      const int gy = B.y0 - kR + r, gx = B.x0 - kR + c;
+      const bool in = k < kHY * kHX && gx >= 0 && gx < B.W && gy >= 0 && gy < B.H;
+      lx[i] = in ? xs[(int64_t)gy * B.W + gx] : 0.0f;
+      ly[i] = in ? ys[(int64_t)gy * B.W + gx] : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < kLd; ++i) {
+      const int k = threadIdx.x + i * 256;
+      if (k < kHY * kHX) {
+        const int r = k / kHX, c = k - r * kHX;
+        s_in[0][r][c] = lx[i];
+        s_in[1][r][c] = ly[i];
+      }
+    }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < kHY * (kTX / kRun); k += blockDim.x) {
@@ -158,7 +173,9 @@ __global__ void __launch_bounds__(256) k_ssim_stats(ViewTable vt, SsimWin win, c
   }
   __syncthreads();
   // vertical pass: column c, rows r0 .. r0 + kRun - 1 from a register window
-  double sum_s = 0.0, sum_l1 = 0.0;
+  // per-thread sums of 4 values in fp32 (GB300's FP64 rate is a small fraction
+  // of FP32); the block and view sums are FP64
+  float sum_s = 0.0f, sum_l1 = 0.0f;
   {
     const int c = threadIdx.x % kTX, r0 = (threadIdx.x / kTX) * kRun;
     float m[5][kRun];
@@ -219,13 +236,28 @@ __global__ void __launch_bounds__(256) k_ssim_grad(ViewTable vt, SsimWin win, co
   const SsimBlock B = ssim_block(vt, blockIdx.x);
   const int64_t HW = (int64_t)B.W * B.H;
   const int64_t base = 3 * vt.v[B.v].pix_off + B.ch * HW;
-  for (int k = threadIdx.x; k < kHY * kHX; k += blockDim.x) {
+  // all of a thread's halo loads are issued before any store (memory-level
+  // parallelism: the loads are the kernel's latency)
+  constexpr int kLd = (kHY * kHX + 255) / 256;
+  float ld[kLd][3];
+#pragma unroll
+  for (int i = 0; i < kLd; ++i) {
+    const int k = threadIdx.x + i * 256;
     const int r = k / kHX, c = k - r * kHX;
     const int gy = B.y0 - kR + r, gx = B.x0 - kR + c;
-    const bool in = gx >= 0 && gx < B.W && gy >= 0 && gy < B.H;
+    const bool in = k < kHY * kHX && gx >= 0 && gx < B.W && gy >= 0 && gy < B.H;
     const int64_t at = base + (int64_t)gy * B.W + gx;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) s_m[q][r][c] = in ? abc[q * plane + at] : 0.0f;
+    for (int q = 0; q < 3; ++q) ld[i][q] = in ? abc[q * plane + at] : 0.0f;
+  }
+#pragma unroll
+  for (int i = 0; i < kLd; ++i) {
+    const int k = threadIdx.x + i * 256;
+    if (k < kHY * kHX) {
+      const int r = k / kHX, c = k - r * kHX;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s_m[q][r][c] = ld[i][q];
+    }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < kHY * (kTX / kRun); k += blockDim.x) {
@@ -276,7 +308,6 @@ __global__ void __launch_bounds__(256) k_ssim_grad(ViewTable vt, SsimWin win, co
 // per view: the sums of its blocks' partials (fixed order), then the loss
 __global__ void __launch_bounds__(256) k_ssim_loss(ViewTable vt, const double* __restrict__ acc, int nb,
                                                    float lambda, float* __restrict__ loss) {
-  __shared__ double s_w[8];
   const int v = blockIdx.x;
   const int b0 = vt.v[v].pad0, b1 = v + 1 < vt.n_views ? vt.v[v + 1].pad0 : nb;
   double ss = 0.0, sl = 0.0;
@@ -284,9 +315,17 @@ __global__ void __launch_bounds__(256) k_ssim_loss(ViewTable vt, const double* _
     ss += acc[2 * b];
     sl += acc[2 * b + 1];
   }
-  const double ts = block_sum_d(ss, s_w);
+  // one CTA per view: FP64 throughout (a few thousand values)
+  __shared__ double s_a[256], s_b[256];
+  s_a[threadIdx.x] = ss;
+  s_b[threadIdx.x] = sl;
   __syncthreads();
-  const double tl = block_sum_d(sl, s_w);
+  double ts = 0.0, tl = 0.0;
+  if (threadIdx.x == 0)
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      ts += s_a[t];
+      tl += s_b[t];
+    }
   if (threadIdx.x == 0) {
     const double n = 3.0 * (double)vt.v[v].width * vt.v[v].height;
     loss[v] = (float)((1.0 - lambda) * tl / n + lambda * (1.0 - ts / n));
