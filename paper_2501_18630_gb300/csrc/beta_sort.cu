@@ -119,9 +119,9 @@ __global__ void k_sort_prep(uint32_t* ghist, uint32_t* counters, unsigned long l
 }
 
 // Adds one key per lane to the per-pass digit histograms (BITS-bit digits).
-// Per pass, two rounds of "broadcast a leader's digit, count its peers": a
-// digit shared by most of the warp costs one shared-memory atomic; the few
-// lanes left add themselves (spread digits rarely collide).  Warp-uniform call.
+// Per pass, the leader's digit and its peers cost one shared-memory atomic,
+// the other lanes add themselves (a second leader round measured slower:
+// spread digits rarely share).  Warp-uniform call.
 template <int BITS>
 __device__ __forceinline__ void hist_add(uint32_t k, bool valid, int npass, uint32_t (*h)[1 << BITS],
                                          int lane) {
@@ -130,17 +130,13 @@ __device__ __forceinline__ void hist_add(uint32_t k, bool valid, int npass, uint
   if (vmask == 0u) return;
   for (int p = 0; p < npass; ++p) {
     const uint32_t d = (k >> (BITS * p)) & kMask;
-    uint32_t left = vmask;
-#pragma unroll
-    for (int round = 0; round < 2; ++round) {
-      if (left == 0u) break;
-      const int leader = __ffs(left) - 1;
-      const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
-      const uint32_t peers = __ballot_sync(0xffffffffu, valid && d == dl) & left;
-      if (lane == leader) atomicAdd(&h[p][dl], (uint32_t)__popc(peers));
-      left &= ~peers;
-    }
-    if ((left >> lane) & 1u) atomicAdd(&h[p][d], 1u);
+    // the leader's digit and its peers: one atomic (a digit most of the warp
+    // shares, as in the depth keys' top bytes); the rest add themselves
+    const int leader = __ffs(vmask) - 1;
+    const uint32_t dl = __shfl_sync(0xffffffffu, d, leader);
+    const uint32_t peers = __ballot_sync(0xffffffffu, valid && d == dl);
+    if (lane == leader) atomicAdd(&h[p][dl], (uint32_t)__popc(peers));
+    if (valid && d != dl) atomicAdd(&h[p][d], 1u);
   }
 }
 
