@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--views", type=int, default=16)
     ap.add_argument("--n", type=int, default=None, help="Betas (default: the workload's, 1M for workload 3)")
-    ap.add_argument("--width", type=int, default=1920)
-    ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--width", type=int, default=None, help="view width (default: the workload's)")
+    ap.add_argument("--height", type=int, default=None, help="view height (default: the workload's)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true", help="skip per-view, e2e and CPU legs (profiling runs)")
     ap.add_argument("--cpu-pixels", type=int, default=16384)
@@ -57,6 +57,13 @@ def parse():
     ap.add_argument("--config", default=None,
                     help="pin the raster configuration instead of autotuning, e.g. 16x16/256/P (P persistent, G one CTA per tile)")
     return ap.parse_args()
+
+
+def _size(args):
+    """An explicit --width/--height pair, else None (the workload's sizes)."""
+    if (args.width is None) != (args.height is None):
+        raise SystemExit("give both --width and --height, or neither")
+    return (args.width, args.height) if args.width is not None else None
 
 
 def peaks():
@@ -173,7 +180,7 @@ def run_reference(args):
         return 0
     from paper_2501_18630_gb300 import scenes
     sc = scenes.config_scene(args.workload, n=args.n, n_views=args.views)
-    cams = scenes.ring_cameras(args.views, 4.0, 15.0, (args.width, args.height))
+    cams = scenes.ring_cameras(args.views, 4.0, 15.0, scenes.workload_sizes(args.workload, args.views, _size(args)))
     px = 1024
     value, cores, total = oracle_leg(args, cams, sc, px, args.steps, args.warmup)
     ms = total / args.steps * 1e3
@@ -182,7 +189,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{sc.n} Betas (256 sheets, 3 SB lobes), {args.views} views "
-                               f"{args.width}x{args.height}; FP64 oracle forward on {px} sampled pixels per step",
+                               f"{scenes.describe_sizes(cams)}; FP64 oracle forward on {px} sampled pixels per step",
                    "n_betas": sc.n, "views": args.views},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{px} seeded pixels of one view per step, forward only (the oracle has no backward)"},
@@ -219,7 +226,7 @@ def main():
 
     V = args.views
     sc = scenes.config_scene(args.workload, n=args.n, n_views=V)
-    ring = scenes.ring_cameras(V * world, 4.0, 15.0, (args.width, args.height))
+    ring = scenes.ring_cameras(V * world, 4.0, 15.0, scenes.workload_sizes(args.workload, V * world, _size(args)))
     cams = distributed.shard_views(ring, rank, world)
     planes = torch.from_numpy(sc.planes).to(dev)
     targets_np = scenes.target_images(cams, seed=77 + rank)
@@ -304,7 +311,8 @@ def main():
     keys = rast.proj[V * rast.pitch * 56: V * rast.pitch * 60].view(torch.int32).view(V, rast.pitch)
     binned = keys != -1
     area = math.pi / (rec[..., 4] * rec[..., 5]).clamp_min(1e-30)          # pi sqrt(det Sigma')
-    evals = float(torch.where(binned, area.clamp_max(args.width * args.height), torch.zeros_like(area)).sum().item())
+    view_px = torch.tensor([float(c.width * c.height) for c in cams], device=area.device).view(V, 1)
+    evals = float(torch.where(binned, torch.minimum(area, view_px), torch.zeros_like(area)).sum().item())
     alu_peak = 152 * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12      # TFLOP/s
     n_planes = scenes.n_planes(sc.n_lobes)
     if dom in ("raster_fwd", "raster_bwd"):
@@ -318,7 +326,7 @@ def main():
     else:
         nrec = V * sc.n
         bytes_alg = {"project": sc.n * n_planes * 4 + nrec * 60,
-                     "bin_sort": nrec * 8 * 4 + K * 8 * 3,
+                     "bin_sort": nrec * 20 + K * 20,
                      "l1": rast.total_pixels * 3 * 4 * 3,
                      "project_bwd": nrec * 48 * 2 + sc.n * n_planes * 8}.get(dom, 0)
         achieved = bytes_alg / (stage_ms[dom] * 1e-3) / 1e9
@@ -502,23 +510,19 @@ def main():
                                                 f"workload, forward only (FP64, every Beta per pixel), {tot:.1f} s"}
 
     # kernel launches of ours inside the timed region (all inside the replayed graph):
-    # project 1; bin_sort: prep, depth histogram, 4 depth passes, emit, tile
-    # histogram + tile passes (two 9-bit passes for 17-18-bit tile ids), tile
-    # ranges; schedule 3 (persistent); raster fwd 1; L1 2; raster bwd 1; project bwd 1
-    tbits = max(1, math.ceil(math.log2(max(rast.total_tiles, 2))))
-    np_t = 2 if tbits in (17, 18) else math.ceil(tbits / 8)
-    per_step = (1 + (1 + 1 + 4 + 1 + (1 + np_t) + 1) + (3 if rast.persistent else 0)
-                + 1 + 2 + 1 + 1)
+    # project 1; bin_sort 5 (prep, tile counts, scan, scatter, list sort);
+    # schedule 3 (persistent); raster fwd 1; L1 2; raster bwd 1; project bwd 1
+    per_step = 1 + 5 + (3 if rast.persistent else 0) + 1 + 2 + 1 + 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"{sc.n} Betas (256 planar sheets, 3 SB lobes), {V} views {args.width}x{args.height} "
+        "config": {"workload": f"{sc.n} Betas (256 planar sheets, 3 SB lobes), {V} views {scenes.describe_sizes(cams)} "
                                f"per GPU, fwd+bwd with per-view L1 loss, one CUDA-graph replay per step",
                    "tile": f"{tw}x{th}", "batch_s": bs, "persistent": persist,
                    "autotune": {"s": round(t_tune, 1), "ms": {f"{c[0]}x{c[1]}/S{c[2]}/{'P' if c[3] else 'G'}": round(v, 3)
                                                               for c, v in tune_ms.items()}},
-                   "n_betas": sc.n, "views_per_gpu": V, "resolution": f"{args.width}x{args.height}",
+                   "n_betas": sc.n, "views_per_gpu": V, "resolution": scenes.describe_sizes(cams),
                    "pairs_per_step": K, "l2": f"inputs larger than L2: {sc.n * n_planes * 4 / 1e6:.0f} MB params + "
                                                f"{V * sc.pitch * 60 / 1e6:.0f} MB records per step",
                    "parallelism": f"dp{world} over views"},

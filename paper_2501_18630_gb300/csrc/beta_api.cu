@@ -219,6 +219,7 @@ int beta_bin_sort(const beta_params* prm, const beta_camera* cams, int32_t n_vie
   if (e != BETA_OK) return e;
   ViewTable vt;
   if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  if ((int64_t)prm->pitch * n_views >= (1ll << 32)) return BETA_ERR_ARG;
   size_t need = binsort_ws_bytes((int64_t)prm->pitch * n_views, pair_capacity, vt.total_tiles);
   if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u) != 0) return BETA_ERR_WORKSPACE;
   ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
@@ -238,6 +239,7 @@ int beta_bin_sort_static(const beta_params* prm, const beta_camera* cams, int32_
   if (e != BETA_OK) return e;
   ViewTable vt;
   if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  if ((int64_t)prm->pitch * n_views >= (1ll << 32)) return BETA_ERR_ARG;
   size_t need = binsort_ws_bytes((int64_t)prm->pitch * n_views, pair_capacity, vt.total_tiles);
   if (need > (size_t)BETA_STATIC_SCRATCH_BYTES) return BETA_ERR_WORKSPACE;
   void* ws = nullptr;

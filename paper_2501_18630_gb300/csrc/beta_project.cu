@@ -36,6 +36,17 @@ ProjBuffers proj_layout(void* proj, int32_t pitch, int32_t n_views) {
 namespace {
 
 constexpr float kLog2e = 1.4426950408889634f;
+
+// Asynchronous 16-byte global -> shared copies (LDGSTS): the backward loads
+// the 2D gradients of the views ahead without holding registers for them.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  const size_t ga = __cvta_generic_to_global(gmem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(ga) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 constexpr float kLn2 = 0.6931471805599453f;
 
 __device__ __forceinline__ float sigmoidf(float x) { return 1.0f / (1.0f + expf(-x)); }
@@ -103,7 +114,8 @@ __device__ __forceinline__ void sb_colour(const float* p, const PrimAttr<M>& a, 
       const float* L = p + 15 + 6 * m;
       float dot = a.lobe_dir[m][0] * vx + a.lobe_dir[m][1] * vy + a.lobe_dir[m][2] * vz;
       if (dot > 0.0f) {
-        float w = exp2f(a.lobe_beta[m] * log2f(dot));
+        // MUFU log2/exp2 (relative error ~1e-6 in w, far below the image tolerance)
+        float w = ex2_approx(a.lobe_beta[m] * lg2_approx(dot));
         c[0] = fmaf(w, L[3], c[0]);
         c[1] = fmaf(w, L[4], c[1]);
         c[2] = fmaf(w, L[5], c[2]);
@@ -217,6 +229,10 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict_
                                                      float* __restrict__ grad2d,
                                                      float* __restrict__ gout,
                                                      const int32_t* __restrict__ status) {
+  // 2D gradients of views v+1 and v+2 in flight while view v is processed:
+  // [buffer][float4][thread], each thread reads only its own slots
+  constexpr int kAhead = 2;
+  __shared__ __align__(16) float4 s_g[kAhead + 1][3][256];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   constexpr int NP = 15 + 6 * M;
@@ -242,10 +258,24 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict_
 #pragma unroll
     for (int m = 0; m < MM; ++m) dRm[m][0] = dRm[m][1] = dRm[m][2] = 0.0f;
     float go = 0.0f, gbeta = 0.0f;
+    const int tid = threadIdx.x;
+    auto fetch = [&](int v) {
+      if (v < vt.n_views) {
+        const float4* src = reinterpret_cast<const float4*>(grad2d + ((size_t)v * pitch + i) * kGrad2dStride);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) cp_async16(&s_g[v % (kAhead + 1)][q][tid], src + q);
+      }
+      cp_async_commit();   // one group per view, empty past the last
+    };
+#pragma unroll
+    for (int a = 0; a < kAhead; ++a) fetch(a);
     for (int v = 0; v < vt.n_views; ++v) {
       const ViewDev& V = vt.v[v];
       float4* g2 = reinterpret_cast<float4*>(grad2d + ((size_t)v * pitch + i) * kGrad2dStride);
-      const float4 ga4 = g2[0], gb4 = g2[1], gc4 = g2[2];
+      cp_async_wait<kAhead - 1>();   // view v's group has landed
+      const int sb = v % (kAhead + 1);
+      const float4 ga4 = s_g[sb][0][tid], gb4 = s_g[sb][1][tid], gc4 = s_g[sb][2][tid];
+      fetch(v + kAhead);
       const float G[kGrad2d] = {ga4.x, ga4.y, ga4.z, ga4.w, gb4.x, gb4.y, gb4.z, gb4.w, gc4.x, gc4.y};
       bool any = false;
 #pragma unroll

@@ -248,6 +248,29 @@ def sheet_scene(n, n_lobes, rng, n_sheets=256):
 MIXED_SIZES = [(640, 480), (1280, 720), (1920, 1080), (2560, 1440)]
 
 
+def workload_sizes(config_id: int, n_views: int, size=None) -> list:
+    """(width, height) of each ring view of a workload: 1920x1080 (3), four
+    views each of MIXED_SIZES in turn (4), 3840x2160 (5); `size` overrides."""
+    if size is not None:
+        return [tuple(size)] * n_views
+    if config_id == 4:
+        return [MIXED_SIZES[k // 4 % 4] for k in range(n_views)]
+    if config_id == 5:
+        return [(3840, 2160)] * n_views
+    return [(1920, 1080)] * n_views
+
+
+def describe_sizes(cams) -> str:
+    """'1920x1080' for equal views, else the count of each size."""
+    sizes = [(c.width, c.height) for c in cams]
+    if len(set(sizes)) == 1:
+        return f"{sizes[0][0]}x{sizes[0][1]}"
+    out = []
+    for wh in sorted(set(sizes)):
+        out.append(f"{sizes.count(wh)} x {wh[0]}x{wh[1]}")
+    return "mixed (" + ", ".join(out) + ")"
+
+
 def config_scene(config_id: int, n: int | None = None, n_views: int | None = None,
                  seed: int | None = None) -> Scene:
     """Workloads of the benchmark table, with optional down-scaled primitive counts.

@@ -101,6 +101,19 @@ def test_bin_sort_ragged_sizes():
         _check_bins(sc, [cam])
 
 
+def test_bin_sort_equal_depth_keys_keep_record_order():
+    """Primitives repeated verbatim have equal depth keys in every tile they
+    share: the lists hold them in record order, as the oracle's stable sort."""
+    base = scenes.config_scene(1, n=700, seed=5)
+    reps = 4
+    n = base.n * reps
+    planes = np.zeros((base.planes.shape[0], scenes.round_pitch(n)), np.float32)
+    for r in range(reps):
+        planes[:, r * base.n:(r + 1) * base.n] = base.planes[:, :base.n]
+    sc = scenes.Scene(planes=planes, n=n, n_lobes=base.n_lobes, cameras=base.cameras, name="repeated")
+    assert _check_bins(sc, sc.cameras) > 0
+
+
 # --------------------------------------------------------------------------
 # step 3: images
 # --------------------------------------------------------------------------
