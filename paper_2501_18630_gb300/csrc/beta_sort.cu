@@ -43,7 +43,7 @@ constexpr int kWarpMax = 512;                      // longest list one warp sort
 constexpr int kCtaItems = 16;
 constexpr int kCtaMax = kSortThreads * kCtaItems;      // longest list sorted in one shared-memory pass
 constexpr int kTicketLists = 4;                    // short lists per warp ticket
-constexpr int kSub = 8;                            // counters per tile (record index mod kSub): spreads
+constexpr int kSub = 16;                           // counters per tile (record index mod kSub): spreads
                                                    // the atomics on a busy tile over kSub addresses
 constexpr int kSpinLimit = 1 << 20;
 constexpr u64 kAgg = 1ull << 62, kInc = 2ull << 62, kCountMask = (1ull << 62) - 1;
