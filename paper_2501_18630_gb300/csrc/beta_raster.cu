@@ -207,19 +207,19 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
           const float u = f1.x * dx;
           const float vv = fmaf(f1.z, dx, f1.y * dy);
           const float r2 = fmaf(u, u, vv * vv);
-          if (!done && r2 < 1.0f) {
-            const float4 f2 = s_rec[buf][s][2];
-            const float lb = lg2_approx(1.0f - r2);
-            float a = ex2_approx(fmaf(f1.w, lb, f2.x));
-            a = fminf(a, amax);
-            const float w = a * T;
-            C0 = fmaf(w, f2.y, C0);
-            C1 = fmaf(w, f2.z, C1);
-            C2 = fmaf(w, f2.w, C2);
-            T = T * (1.0f - a);
-            last = base - start + (uint32_t)s + 1u;
-            done = T < t_eps;
-          }
+          // evaluated by every lane (no divergent branch); lanes outside the
+          // support or already done add nothing (their garbage is selected away)
+          const bool act = !done && r2 < 1.0f;
+          const float4 f2 = s_rec[buf][s][2];
+          const float lb = lg2_approx(1.0f - r2);
+          const float a = act ? fminf(ex2_approx(fmaf(f1.w, lb, f2.x)), amax) : 0.0f;
+          const float w = a * T;
+          C0 = fmaf(w, f2.y, C0);
+          C1 = fmaf(w, f2.z, C1);
+          C2 = fmaf(w, f2.w, C2);
+          T = T * (1.0f - a);
+          last = act ? base - start + (uint32_t)s + 1u : last;
+          done = T < t_eps;
         }
         warp_done = __all_sync(0xffffffffu, done);
       }
@@ -407,36 +407,34 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
           // per-record constants applied by the projection backward:
           //   G0..G4 = k (u, v, u^2, u v, v^2),  k = (dL/dalpha) alpha / (1 - r^2)
           //   G5 = (dL/dalpha) alpha,  G6 = G5 log2(1 - r^2),  G7..9 = alpha T dL/dC
+          // evaluated by every lane (no divergent branch); only active lanes
+          // update their state and add their values
           float G[kGrad2d];
-#pragma unroll
-          for (int q = 0; q < kGrad2d; ++q) G[q] = 0.0f;
-          if (act) {
-            const float4 f2 = s_rec[buf][s][2];
-            const float beta = f1.w;
-            const float base = 1.0f - r2;
-            const float lb = lg2_approx(base);
-            const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
-            const float a = fminf(a0, amax);
-            const float inv = rcp_approx(1.0f - a);
-            const float Tk = T * inv;
-            const float gc = fmaf(gx, f2.y, fmaf(gy, f2.z, gz * f2.w));
-            const float dLa = fmaf(Tk, gc, -GS * inv);
-            const float wgt = a * Tk;
-            GS = fmaf(wgt, gc, GS);
-            G[7] = wgt * gx;
-            G[8] = wgt * gy;
-            G[9] = wgt * gz;
-            const float t = a0 < amax ? dLa * a0 : 0.0f;         // clamped alpha: no o/beta/r^2 gradient
-            const float kk = t * rcp_approx(base);
-            G[0] = kk * u;
-            G[1] = kk * vv;
-            G[2] = G[0] * u;
-            G[3] = G[0] * vv;
-            G[4] = G[1] * vv;
-            G[5] = t;
-            G[6] = t * lb;
-            T = Tk;
-          }
+          const float4 f2 = s_rec[buf][s][2];
+          const float beta = f1.w;
+          const float base = 1.0f - r2;
+          const float lb = lg2_approx(base);
+          const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
+          const float a = fminf(a0, amax);
+          const float inv = rcp_approx(1.0f - a);
+          const float Tk = T * inv;
+          const float gc = fmaf(gx, f2.y, fmaf(gy, f2.z, gz * f2.w));
+          const float dLa = fmaf(Tk, gc, -GS * inv);
+          const float wgt = a * Tk;
+          G[7] = wgt * gx;
+          G[8] = wgt * gy;
+          G[9] = wgt * gz;
+          const float t = a0 < amax ? dLa * a0 : 0.0f;           // clamped alpha: no o/beta/r^2 gradient
+          const float kk = t * rcp_approx(base);
+          G[0] = kk * u;
+          G[1] = kk * vv;
+          G[2] = G[0] * u;
+          G[3] = G[0] * vv;
+          G[4] = G[1] * vv;
+          G[5] = t;
+          G[6] = t * lb;
+          GS = act ? fmaf(wgt, gc, GS) : GS;
+          T = act ? Tk : T;
           float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
           if (__popc(amask) <= 12) {
             // up to 12 lanes: each adds its ten values with three vector atomics,
@@ -447,6 +445,8 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
               red_add_v4(gdst + 8, G[8], G[9], 0.0f, 0.0f);
             }
           } else {
+#pragma unroll
+            for (int q = 0; q < kGrad2d; ++q) G[q] = act ? G[q] : 0.0f;
             const float tot = warp_sum10(G, lane);
             if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
           }
