@@ -369,18 +369,73 @@ __device__ __forceinline__ void group_merge(u64 (&k)[E], u64* sm, int t) {
   }
 }
 
-// Sorts list items[0, n) (n <= 32 E) with one warp and writes the record ids.
+// Bitonic network across the warp for lane-sorted runs (E registers a lane,
+// item i = lane * E + j): from run size 2E up to 32E, strides >= E exchange
+// with lane ^ (stride / E) through shuffles and strides < E are
+// compare-exchanges inside the lane; a run's direction is bit log2(size) of
+// its first item.  No shared memory and no dependent loads.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(u64 (&k)[E], int lane) {
+  // lane runs must alternate ascending / descending for the first merge
+  if (lane & 1) {
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) {
+      const u64 t = k[j];
+      k[j] = k[E - 1 - j];
+      k[E - 1 - j] = t;
+    }
+  }
+#pragma unroll 1
+  for (int size = 2 * E; size <= 32 * E; size <<= 1) {
+    const bool up = ((lane * E) & size) == 0;
+#pragma unroll 1
+    for (int stride = size >> 1; stride >= E; stride >>= 1) {
+      const int lm = stride / E;
+      const bool take_min = ((lane & lm) == 0) == up;
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const u64 o = __shfl_xor_sync(0xffffffffu, k[j], lm);
+        k[j] = (take_min == (o < k[j])) ? o : k[j];
+      }
+    }
+#pragma unroll
+    for (int stride = E / 2; stride > 0; stride >>= 1)
+#pragma unroll
+      for (int j = 0; j < E; ++j) {
+        const int jj = j ^ stride;
+        if (jj > j) {
+          const u64 a = k[j], b = k[jj];
+          const bool sw = up ? (a > b) : (a < b);
+          k[j] = sw ? b : a;
+          k[jj] = sw ? a : b;
+        }
+      }
+  }
+}
+
+// Sorts list items[0, n) (n <= 32 E) with one warp and writes the record ids:
+// E <= 8 by the shuffle network, E = 16 by merge-path merges in shared memory.
 template <int E>
 __device__ __forceinline__ void warp_list_sort(const u64* items, int n, uint32_t* __restrict__ out,
                                                u64* sm, int lane) {
-  for (int p = lane; p < 32 * E; p += 32) sm[sidx(p)] = p < n ? items[p] : kPad;
-  __syncwarp();
   u64 k[E];
+  if (E <= 8) {
 #pragma unroll
-  for (int j = 0; j < E; ++j) k[j] = sm[sidx(lane * E + j)];
-  __syncwarp();
-  sort_regs<E>(k);
-  group_merge<32, E>(k, sm, lane);
+    for (int j = 0; j < E; ++j) {
+      const int p = lane * E + j;
+      k[j] = p < n ? items[p] : kPad;
+    }
+    sort_regs<E>(k);
+    warp_bitonic<E>(k, lane);
+  } else {
+    for (int p = lane; p < 32 * E; p += 32) sm[sidx(p)] = p < n ? items[p] : kPad;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < E; ++j) k[j] = sm[sidx(lane * E + j)];
+    __syncwarp();
+    sort_regs<E>(k);
+    group_merge<32, E>(k, sm, lane);
+  }
 #pragma unroll
   for (int j = 0; j < E; ++j) sm[sidx(lane * E + j)] = k[j];
   __syncwarp();
@@ -507,7 +562,8 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_tile_sort(const uint32_t* _
         continue;
       }
       if (n > kWarpMax) continue;
-      if (n <= 64) warp_list_sort<2>(items + s, n, vals + s, wsm, lane);
+      if (n <= 32) warp_list_sort<1>(items + s, n, vals + s, wsm, lane);
+      else if (n <= 64) warp_list_sort<2>(items + s, n, vals + s, wsm, lane);
       else if (n <= 128) warp_list_sort<4>(items + s, n, vals + s, wsm, lane);
       else if (n <= 256) warp_list_sort<8>(items + s, n, vals + s, wsm, lane);
       else warp_list_sort<16>(items + s, n, vals + s, wsm, lane);
