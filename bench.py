@@ -37,7 +37,8 @@ UNIT = "Mpixel/s"
 FWD_FLOPS_PER_EVAL = 24   # r^2 (11), 1 - r^2, beta lg2 + log2 o, min, T alpha, C += (6), T update
 BWD_FLOPS_PER_EVAL = 60   # recompute alpha, T recovery, dL/dalpha, 10 gradient terms
 FP32_LANES_PER_SM = 128
-STAGES = ["project", "bin_sort", "raster_fwd", "l1", "raster_bwd", "project_bwd"]
+# raster_fwd includes the per-view L1 loss (computed in the forward's epilogue)
+STAGES = ["project", "bin_sort", "raster_fwd", "raster_bwd", "project_bwd"]
 
 
 def parse():
@@ -296,10 +297,9 @@ def main():
         if rast.persistent:
             rast.schedule()
         ev[2].record(stream)
-        rast.raster_fwd(planes); ev[3].record(stream)
-        rast.l1_loss(target); ev[4].record(stream)
-        rast.raster_bwd(planes, rast.dL_dcolor); ev[5].record(stream)
-        rast.project_bwd(planes, grad); ev[6].record(stream)
+        rast.raster_fwd_l1(planes, target); ev[3].record(stream)
+        rast.raster_bwd(planes, rast.dL_dcolor); ev[4].record(stream)
+        rast.project_bwd(planes, grad); ev[5].record(stream)
         torch.cuda.synchronize()
         for k, s in enumerate(STAGES):
             stage_ms[s] += ev[k].elapsed_time(ev[k + 1]) / args.steps
@@ -493,9 +493,24 @@ def main():
             t_ss += e0.elapsed_time(e1)
             del flush
         ms_ss = t_ss / args.steps
+        # the L1 term's share of the step: forward with it minus forward without it
+        t_fl = {"plain": 0.0, "l1": 0.0}
+        for _ in range(args.steps):
+            for kind in ("plain", "l1"):
+                flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev).fill_(1.0)
+                e0.record(stream)
+                if kind == "plain":
+                    rast.raster_fwd(planes)
+                else:
+                    rast.raster_fwd_l1(planes, target)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t_fl[kind] += e0.elapsed_time(e1) / args.steps
+                del flush
+        l1_ms = max(0.0, t_fl["l1"] - t_fl["plain"])
         ss_bytes = rast.total_pixels * 3 * 44
         extras["dssim_loss"] = {
-            "ms": ms_ss, "l1_ms": stage_ms["l1"], "step_ms_with_dssim": ms_step - stage_ms["l1"] + ms_ss,
+            "ms": ms_ss, "l1_ms": l1_ms, "step_ms_with_dssim": ms_step - l1_ms + ms_ss,
             "algorithmic_bytes": ss_bytes, "achieved_gbs": ss_bytes / (ms_ss * 1e-3) / 1e9,
             "frac_of_measured_hbm": ss_bytes / (ms_ss * 1e-3) / 1e9 / hbm_peak,
             "what": "beta_l1_dssim_loss, lambda 0.2: Gaussian-window SSIM statistics, loss and gradient "
@@ -512,7 +527,7 @@ def main():
     # kernel launches of ours inside the timed region (all inside the replayed graph):
     # project 1; bin_sort 5 (prep, tile counts, scan, scatter, list sort);
     # schedule 3 (persistent); raster fwd 1; L1 2; raster bwd 1; project bwd 1
-    per_step = 1 + 5 + (3 if rast.persistent else 0) + 1 + 2 + 1 + 1
+    per_step = 1 + 5 + (3 if rast.persistent else 0) + 2 + 1 + 1
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -205,6 +205,25 @@ int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
                     const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
                     uint32_t* n_contrib, const int32_t* d_status, beta_stream_t stream);
 
+/* beta_raster_fwd followed by beta_l1_loss in one pass: the forward kernel
+ * computes the L1 term and dL_dcolor of each pixel it writes, and one partial
+ * sum per tile, which a second kernel adds per view in tile order.  Outputs
+ * color, T_final, n_contrib as beta_raster_fwd, and loss, dL_dcolor as
+ * beta_l1_loss (dL_dcolor bit for bit; loss to fp32 summation order).
+ *   target   [3 x total_pixels] in (layout of color)
+ *   loss     device float[n_views] out;  dL_dcolor: layout of color, out
+ *   ws       beta_raster_fwd_l1_workspace_bytes() bytes (one float per tile),
+ *            4-byte aligned
+ * Returns BETA_ERR_ARG for null pointers, BETA_ERR_WORKSPACE for a short or
+ * misaligned ws. */
+size_t beta_raster_fwd_l1_workspace_bytes(const beta_camera* cams /* host */, int32_t n_views,
+                                          const beta_opts* opt);
+int beta_raster_fwd_l1(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                       const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
+                       const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
+                       uint32_t* n_contrib, const float* target, float* loss, float* dL_dcolor,
+                       void* ws, size_t ws_bytes, const int32_t* d_status, beta_stream_t stream);
+
 /* Per-pixel L1 loss of a batch of views (Sec. 3.4, the L1 term):
  *   loss[v] = mean over 3 W_v H_v of |color - target|   (device float[n_views], out)
  *   dL_dcolor = sign(color - target) / (3 W_v H_v)       (same layout as color, out)

@@ -1,8 +1,8 @@
 """Batched forward + backward of many views as one replayable CUDA graph.
 
 The whole step -- project, bin/sort, longest-first schedule, persistent
-raster forward, per-view L1 loss, persistent raster backward, projection
-backward -- is captured once and replayed.  Every entry point only enqueues
+raster forward with the per-view L1 loss in its epilogue, persistent raster
+backward, projection backward -- is captured once and replayed.  Every entry point only enqueues
 kernels and the pair count stays on the device, so nothing in the step
 synchronises with the host.  A pair-capacity overflow shows up in the device
 status word; check() reads it (one sync), grows the buffers and recaptures.
@@ -42,8 +42,7 @@ class BatchedStep:
         r.bin_sort(self.planes)
         if r.persistent:
             r.schedule()
-        r.raster_fwd(self.planes)
-        r.l1_loss(self.target)
+        r.raster_fwd_l1(self.planes, self.target)
         r.raster_bwd(self.planes, r.dL_dcolor)
         r.project_bwd(self.planes, self.grad)
 

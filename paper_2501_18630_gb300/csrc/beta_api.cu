@@ -267,6 +267,32 @@ int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
                                        (cudaStream_t)stream));
 }
 
+size_t beta_raster_fwd_l1_workspace_bytes(const beta_camera* cams, int32_t n_views, const beta_opts* opt) {
+  ViewTable vt;
+  if (check_opts(opt) != BETA_OK || build_views(cams, n_views, opt, vt) != BETA_OK) return 0;
+  return fwd_l1_ws_bytes(vt);
+}
+
+int beta_raster_fwd_l1(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                       const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
+                       const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
+                       uint32_t* n_contrib, const float* target, float* loss, float* dL_dcolor,
+                       void* ws, size_t ws_bytes, const int32_t* d_status, beta_stream_t stream) {
+  if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !color || !T_final ||
+      !n_contrib || !d_status || !target || !loss || !dL_dcolor)
+    return BETA_ERR_ARG;
+  int e = check_opts(opt);
+  if (e != BETA_OK) return e;
+  ViewTable vt;
+  if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  if (sched && ((uintptr_t)sched & 3u)) return BETA_ERR_ARG;
+  if (!ws || ws_bytes < fwd_l1_ws_bytes(vt) || ((uintptr_t)ws & 3u)) return BETA_ERR_WORKSPACE;
+  ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
+  return cuda_status(launch_raster_fwd_l1(vt, render_opts(opt), pb.rec, pair_vals, tile_ranges, color,
+                                          T_final, n_contrib, d_status, (uint32_t*)sched, target, loss,
+                                          dL_dcolor, (float*)ws, (cudaStream_t)stream));
+}
+
 size_t beta_schedule_bytes(const beta_camera* cams, int32_t n_views, const beta_opts* opt) {
   ViewTable vt;
   if (check_opts(opt) != BETA_OK || build_views(cams, n_views, opt, vt) != BETA_OK) return 0;

@@ -366,6 +366,12 @@ cudaError_t launch_raster_bwd(const ViewTable& vt, const RenderOpts& ro, const f
 size_t schedule_bytes(int total_tiles);
 cudaError_t launch_schedule(const ViewTable& vt, const uint32_t* ranges, uint32_t* sched,
                             const int32_t* status, cudaStream_t s);
+size_t fwd_l1_ws_bytes(const ViewTable& vt);
+cudaError_t launch_raster_fwd_l1(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
+                                 const uint32_t* vals, const uint32_t* ranges, float* color,
+                                 float* T_final, uint32_t* n_contrib, const int32_t* status,
+                                 uint32_t* sched, const float* target, float* loss, float* dL_dcolor,
+                                 float* ws, cudaStream_t s);
 size_t l1_ws_bytes(const ViewTable& vt);
 cudaError_t launch_l1(const ViewTable& vt, const float* color, const float* target, float* loss,
                       float* dL_dcolor, float* ws, cudaStream_t s);

@@ -138,9 +138,13 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
                                                        float* __restrict__ Tout,
                                                        uint32_t* __restrict__ ncontrib,
                                                        const int32_t* __restrict__ status,
-                                                       uint32_t* ctr, const uint32_t* __restrict__ order) {
+                                                       uint32_t* ctr, const uint32_t* __restrict__ order,
+                                                       const float* __restrict__ target,
+                                                       float* __restrict__ dLdC,
+                                                       float* __restrict__ l1_partial) {
   constexpr int NT = TW * TH, BXW = TW / 8, RPT = (S + NT - 1) / NT;
   __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
+  __shared__ float s_l1[NT / 32];
   __shared__ int s_item;
   if (*status != 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -226,15 +230,40 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
       buf ^= 1;
     }
     cp_async_wait_all();   // no copy may still land in a buffer the next tile fills
+    float l1 = 0.0f;
     if (inside) {
       const int64_t HW = (int64_t)W * H;
       const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
-      float* cb = color + 3 * vt.v[v].pix_off + (int64_t)y * W + x;
-      cb[0] = C0 + T * vt.v[v].bg[0];
-      cb[HW] = C1 + T * vt.v[v].bg[1];
-      cb[2 * HW] = C2 + T * vt.v[v].bg[2];
+      const int64_t o = 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+      const float c[3] = {C0 + T * vt.v[v].bg[0], C1 + T * vt.v[v].bg[1], C2 + T * vt.v[v].bg[2]};
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) color[o + ch * HW] = c[ch];
       Tout[pix] = T;
       ncontrib[pix] = last;
+      if (target) {
+        // the per-pixel L1 term and its gradient, as beta_l1_loss computes them
+        const float scale = 1.0f / (3.0f * (float)HW);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          const float d = c[ch] - target[o + ch * HW];
+          l1 += fabsf(d);
+          dLdC[o + ch * HW] = d > 0.0f ? scale : (d < 0.0f ? -scale : 0.0f);
+        }
+      }
+    }
+    if (target) {
+      // tile partial sum of |C - target|, reduced in a fixed order
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+      if (lane == 0) s_l1[warp] = l1;
+      __syncthreads();
+      if (tid == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) t += s_l1[w];
+        l1_partial[g] = t;
+      }
+      __syncthreads();
     }
   }
   leave<PERSIST>(ctr);
@@ -604,14 +633,17 @@ int persistent_grid(K kernel, int threads, int total_tiles) {
 template <int TW, int TH, int S>
 cudaError_t fwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                       const uint32_t* vals, const uint32_t* ranges, float* color, float* T_final,
-                      uint32_t* n_contrib, const int32_t* status, uint32_t* sched, cudaStream_t s) {
+                      uint32_t* n_contrib, const int32_t* status, uint32_t* sched, const float* target,
+                      float* dL_dcolor, float* l1_partial, cudaStream_t s) {
   if (sched) {
     auto k = k_raster_fwd<TW, TH, S, true>;
     k<<<persistent_grid(k, TW * TH, vt.total_tiles), TW * TH, 0, s>>>(
-        vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched + 0, sched + kSchedOrder);
+        vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched + 0, sched + kSchedOrder,
+        target, dL_dcolor, l1_partial);
   } else {
     k_raster_fwd<TW, TH, S, false><<<vt.total_tiles, TW * TH, 0, s>>>(
-        vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, nullptr, nullptr);
+        vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, nullptr, nullptr, target, dL_dcolor,
+        l1_partial);
   }
   return cudaGetLastError();
 }
@@ -664,7 +696,30 @@ cudaError_t launch_raster_fwd(const ViewTable& vt, const RenderOpts& ro, const f
                               float* T_final, uint32_t* n_contrib, const int32_t* status,
                               uint32_t* sched, cudaStream_t s) {
   if (vt.total_tiles <= 0) return cudaSuccess;
-  BETA_TILE_DISPATCH(fwd_shape, vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched, s)
+  BETA_TILE_DISPATCH(fwd_shape, vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched,
+                     nullptr, nullptr, nullptr, s)
+}
+
+size_t fwd_l1_ws_bytes(const ViewTable& vt) { return (size_t)std::max(vt.total_tiles, 1) * sizeof(float); }
+
+// Forward with the L1 loss in its epilogue: the kernel writes dL/dC and one
+// partial sum per tile; k_l1_reduce then sums each view's tiles in order.
+cudaError_t launch_raster_fwd_l1(const ViewTable& vt_in, const RenderOpts& ro, const float4* rec,
+                                 const uint32_t* vals, const uint32_t* ranges, float* color,
+                                 float* T_final, uint32_t* n_contrib, const int32_t* status,
+                                 uint32_t* sched, const float* target, float* loss, float* dL_dcolor,
+                                 float* ws, cudaStream_t s) {
+  if (vt_in.total_tiles <= 0) return cudaSuccess;
+  cudaError_t e = [&]() -> cudaError_t {
+    const ViewTable& vt = vt_in;
+    BETA_TILE_DISPATCH(fwd_shape, vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched,
+                       target, dL_dcolor, ws, s)
+  }();
+  if (e != cudaSuccess) return e;
+  ViewTable vt = vt_in;   // the reduce finds view v's partials from tile_off[v]
+  for (int v = 0; v < vt.n_views; ++v) vt.v[v].pad0 = vt.v[v].tile_off;
+  k_l1_reduce<<<vt.n_views, 256, 0, s>>>(vt, ws, vt.total_tiles, loss);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_raster_bwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,

@@ -58,6 +58,8 @@ class Rasterizer:
         self.loss = torch.zeros(self.V, dtype=torch.float32, device=dev)
         self.dL_dcolor = torch.empty_like(self.color)
         self.l1_ws = torch.empty(max(4, int(L.beta_l1_workspace_bytes(self.cams, self.V))), dtype=torch.uint8, device=dev)
+        nb = int(L.beta_raster_fwd_l1_workspace_bytes(self.cams, self.V, ctypes.byref(self.opts)))
+        self.fwd_l1_ws = torch.empty(max(4, nb), dtype=torch.uint8, device=dev)
         cap = pair_capacity if pair_capacity is not None else max(1 << 16, 4 * self.n * self.V)
         self._alloc_pairs(cap)
         self.persistent = bool(persistent)
@@ -115,6 +117,17 @@ class Rasterizer:
             ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
             _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), _vp(self.color),
             _vp(self.T_final), _vp(self.n_contrib), _vp(self.status), _stream()))
+
+    def raster_fwd_l1(self, planes, target: torch.Tensor):
+        """raster_fwd and l1_loss in one pass (the L1 term in the forward's epilogue)."""
+        assert target.numel() == self.color.numel() and target.is_contiguous()
+        prm = self.params(planes)
+        _lib.check("beta_raster_fwd_l1", self.L.beta_raster_fwd_l1(
+            ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
+            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), _vp(self.color),
+            _vp(self.T_final), _vp(self.n_contrib), _vp(target), _vp(self.loss), _vp(self.dL_dcolor),
+            _vp(self.fwd_l1_ws), self.fwd_l1_ws.numel(), _vp(self.status), _stream()))
+        return self.loss, self.dL_dcolor
 
     def l1_loss(self, target: torch.Tensor):
         assert target.numel() == self.color.numel() and target.is_contiguous()

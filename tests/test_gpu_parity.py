@@ -364,3 +364,27 @@ def test_l1_kernel_matches_numpy():
         assert np.allclose(d[seg], np.sign(diff) / (3 * hw), rtol=1e-6, atol=0)
         off += hw
     assert d[5] == 0.0
+
+
+@pytest.mark.parametrize("tile", [(16, 8), (16, 16)])
+def test_forward_with_fused_l1_equals_separate_calls(tile):
+    """beta_raster_fwd_l1 = beta_raster_fwd then beta_l1_loss: the image,
+    T and n_contrib bit for bit, dL/dC bit for bit (the same sign of the same
+    fp32 difference), the per-view loss to fp32 summation order."""
+    sc = scenes.config_scene(4, n=40_000, n_views=8)
+    cams = sc.cameras[::2]                                  # four sizes, ragged edge tiles
+    opts = _lib.default_opts(tile_w=tile[0], tile_h=tile[1])
+    rast, planes = gc.rasterize(sc.planes, sc.n, sc.n_lobes, cams, opts=opts)
+    tgt_np = np.concatenate([t.reshape(-1) for t in scenes.target_images(cams, seed=3)])
+    target = torch.from_numpy(tgt_np).cuda()
+    rast.raster_fwd(planes)
+    loss_a, d_a = (x.clone() for x in rast.l1_loss(target))
+    img_a, T_a, n_a = rast.color.clone(), rast.T_final.clone(), rast.n_contrib.clone()
+    rast.color.zero_(); rast.T_final.zero_(); rast.dL_dcolor.zero_(); rast.loss.zero_()
+    loss_b, d_b = rast.raster_fwd_l1(planes, target)
+    torch.cuda.synchronize()
+    assert torch.equal(rast.color, img_a) and torch.equal(rast.T_final, T_a)
+    assert torch.equal(rast.n_contrib, n_a)
+    assert torch.equal(d_b, d_a)
+    la, lb = loss_a.cpu().numpy().astype(np.float64), loss_b.cpu().numpy().astype(np.float64)
+    assert np.all(la > 0) and np.max(np.abs(la - lb) / la) < 1e-5
