@@ -39,6 +39,7 @@ typedef unsigned long long u64;
 constexpr int kSortThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kSortThreads * kScanItems;   // tiles per scan block
+static_assert(kScanItems == 8, "the scan moves a thread's tiles as two 16-byte vectors");
 constexpr int kWarpMax = 512;                      // longest list one warp sorts (16 items a lane)
 constexpr int kCtaItems = 16;
 constexpr int kCtaMax = kSortThreads * kCtaItems;      // longest list sorted in one shared-memory pass
@@ -54,14 +55,16 @@ constexpr u64 kPad = ~0ull;                        // above every item (depth ke
 constexpr int kCounters = 4;
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+// counter row length: a multiple of kScanItems, so the scan moves 16-byte vectors
+__host__ __device__ inline int64_t crow(int total_tiles) { return cdiv(total_tiles, kScanItems) * kScanItems; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
 // Workspace carve-up (offsets are 256-byte aligned).
 struct SortWs {
-  uint32_t* cnt;       // [kSub][total_tiles] pairs per tile and record class
-  uint32_t* cursor;    // [kSub][total_tiles] next free slot of each class's part of a list
+  uint32_t* cnt;       // [kSub][row] pairs per tile and record class (row = tiles rounded up to 8)
+  uint32_t* cursor;    // [kSub][row] next free slot of each class's part of a list
   uint32_t* longl;     // [total_tiles] tiles whose list is longer than kWarpMax
   u64* look;           // [nb_scan] scan look-back (flag | aggregate or inclusive sum)
   uint32_t* counters;  // [kCounters]
@@ -81,8 +84,8 @@ static SortWs carve(void* base, int64_t cap, int total_tiles) {
   };
   const int64_t nb_scan = cdiv(total_tiles, kScanTile);
   const int64_t c = cap > 0 ? cap : 1;
-  w.cnt = (uint32_t*)take((size_t)kSub * total_tiles * 4);
-  w.cursor = (uint32_t*)take((size_t)kSub * total_tiles * 4);
+  w.cnt = (uint32_t*)take((size_t)kSub * crow(total_tiles) * 4);
+  w.cursor = (uint32_t*)take((size_t)kSub * crow(total_tiles) * 4);
   w.longl = (uint32_t*)take((size_t)total_tiles * 4);
   w.look = (u64*)take((size_t)nb_scan * 8);
   w.counters = (uint32_t*)take(kCounters * 4);
@@ -105,7 +108,7 @@ __global__ void k_sort_prep(uint32_t* cnt, int total_tiles, u64* look, int64_t n
                             uint32_t* counters, int64_t* d_count, int32_t* status) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (int64_t i = t; i < (int64_t)kSub * total_tiles; i += stride) cnt[i] = 0u;
+  for (int64_t i = t; i < (int64_t)kSub * crow(total_tiles); i += stride) cnt[i] = 0u;
   for (int64_t i = t; i < nb_scan; i += stride) look[i] = 0ull;
   if (t < kCounters) counters[t] = 0u;
   if (t == 0) {
@@ -139,11 +142,10 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_count(const uint2* __rest
     if (q.n == 0) continue;
     const int v = (int)((uint32_t)r / (uint32_t)pitch);
     const int ntx = vt.v[v].ntx;
-    uint32_t* c = cnt + (size_t)(r & (kSub - 1)) * total_tiles + vt.v[v].tile_off;
-    for (int j = 0; j < q.n; ++j) {
-      const int dy = j / q.w;
-      atomicAdd(&c[(q.ty0 + dy) * ntx + q.tx0 + (j - dy * q.w)], 1u);
-    }
+    uint32_t* c = cnt + (size_t)(r & (kSub - 1)) * crow(total_tiles) + vt.v[v].tile_off + q.ty0 * ntx + q.tx0;
+    const int h = q.n / q.w;
+    for (int dy = 0; dy < h; ++dy, c += ntx)
+      for (int dx = 0; dx < q.w; ++dx) atomicAdd(&c[dx], 1u);
   }
 }
 
@@ -189,16 +191,24 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scan(const uint32_t* __re
   const int64_t nb = cdiv(total_tiles, kScanTile);
   if (blk >= nb) return;
   const int64_t base = blk * kScanTile + threadIdx.x * kScanItems;
+  // the thread's kScanItems tiles: per class two 16-byte loads (rows are
+  // padded to a multiple of kScanItems and zeroed, so no tail guard)
+  const int64_t row = crow(total_tiles);
+  const bool mine = base < total_tiles;
   uint32_t c[kScanItems];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) c[k] = 0u;
+  if (mine)
+#pragma unroll 4
+    for (int q = 0; q < kSub; ++q) {
+      const uint4* src = reinterpret_cast<const uint4*>(cnt + q * row + base);
+      const uint4 a = src[0], b = src[1];
+      c[0] += a.x; c[1] += a.y; c[2] += a.z; c[3] += a.w;
+      c[4] += b.x; c[5] += b.y; c[6] += b.z; c[7] += b.w;
+    }
   u64 sum = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    c[k] = 0u;
-    if (base + k < total_tiles)
-#pragma unroll
-      for (int q = 0; q < kSub; ++q) c[k] += cnt[(size_t)q * total_tiles + base + k];
-    sum += c[k];
-  }
+  for (int k = 0; k < kScanItems; ++k) sum += c[k];
   u64 total;
   const u64 excl = block_excl_scan(sum, s_w, total);
   if (warp == 0) {
@@ -246,21 +256,28 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scan(const uint32_t* __re
   }
   __syncthreads();
   u64 run = s_base + excl;
+  if (!mine) return;
+  uint32_t start[kScanItems];
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     const int64_t g = base + k;
+    start[k] = (uint32_t)run;
     if (g < total_tiles) {
       ranges[g] = (uint32_t)run;
-      // class q's part of the list starts after classes 0 .. q-1
-      uint32_t at = (uint32_t)run;
-#pragma unroll
-      for (int q = 0; q < kSub; ++q) {
-        cursor[(size_t)q * total_tiles + g] = at;
-        at += cnt[(size_t)q * total_tiles + g];
-      }
       if (c[k] > (uint32_t)kWarpMax) longl[atomicAdd(&counters[3], 1u)] = (uint32_t)g;
     }
     run += c[k];
+  }
+  // class q's part of a list starts after classes 0 .. q-1
+#pragma unroll 4
+  for (int q = 0; q < kSub; ++q) {
+    const uint4* src = reinterpret_cast<const uint4*>(cnt + q * row + base);
+    uint4* dst = reinterpret_cast<uint4*>(cursor + q * row + base);
+    const uint4 a = src[0], b = src[1];
+    dst[0] = make_uint4(start[0], start[1], start[2], start[3]);
+    dst[1] = make_uint4(start[4], start[5], start[6], start[7]);
+    start[0] += a.x; start[1] += a.y; start[2] += a.z; start[3] += a.w;
+    start[4] += b.x; start[5] += b.y; start[6] += b.z; start[7] += b.w;
   }
 }
 
@@ -279,17 +296,20 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scatter(const uint2* __re
     if (q.n == 0) continue;
     const int v = (int)((uint32_t)r / (uint32_t)pitch);
     const int ntx = vt.v[v].ntx;
-    uint32_t* cur = cursor + (size_t)(r & (kSub - 1)) * total_tiles + vt.v[v].tile_off;
+    uint32_t* cur = cursor + (size_t)(r & (kSub - 1)) * crow(total_tiles) + vt.v[v].tile_off;
     const u64 item = ((u64)keys[r] << 32) | (u64)(uint32_t)r;
+    int dx = 0, row = q.ty0 * ntx + q.tx0;   // tile j of the rectangle, row-major, walked incrementally
     for (int j0 = 0; j0 < q.n; j0 += 4) {
       uint32_t slot[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int j = j0 + u;
         slot[u] = 0xffffffffu;
-        if (j < q.n) {
-          const int dy = j / q.w;
-          slot[u] = atomicAdd(&cur[(q.ty0 + dy) * ntx + q.tx0 + (j - dy * q.w)], 1u);
+        if (j0 + u < q.n) {
+          slot[u] = atomicAdd(&cur[row + dx], 1u);
+          if (++dx == q.w) {
+            dx = 0;
+            row += ntx;
+          }
         }
       }
 #pragma unroll
@@ -593,7 +613,7 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
   const int total_tiles = vt.total_tiles;
   SortWs w = carve(ws, cap, total_tiles);
   const int64_t nb_scan = cdiv(total_tiles, kScanTile);
-  const int64_t grid_p = std::min<int64_t>(cdiv(std::max<int64_t>((int64_t)kSub * total_tiles, nb_scan), kSortThreads), 1024);
+  const int64_t grid_p = std::min<int64_t>(cdiv(std::max<int64_t>((int64_t)kSub * crow(total_tiles), nb_scan), kSortThreads), 1024);
   const int64_t grid_r = std::max<int64_t>(1, std::min<int64_t>(cdiv(n_items, kSortThreads), 1 << 20));
 
   k_sort_prep<<<(unsigned)std::max<int64_t>(grid_p, 1), kSortThreads, 0, s>>>(w.cnt, total_tiles, w.look, nb_scan,

@@ -101,6 +101,21 @@ def test_bin_sort_ragged_sizes():
         _check_bins(sc, [cam])
 
 
+def test_bin_sort_lists_longer_than_one_shared_memory_pass():
+    """60k small Betas on a 24x20 image: lists of ~12k (sorted in 4096-item
+    chunks and merged through global memory), ~3.5k, ~1.3k and ~500 items (the
+    CTA sorts of 16, 8 and 4 items a thread) equal the oracle's."""
+    sc = scenes.config_scene(1, n=60_000, seed=12)
+    cam = scenes.pinhole(*scenes.look_at((0.0, 0.0, -3.0)), 24, 20)
+    rast, _ = gc.rasterize(sc.planes, sc.n, sc.n_lobes, [cam])
+    K, ranges, vals = gc.sorted_pairs(rast)
+    _, recs, oranges = oracle.bin_pairs(sc.planes, sc.n, sc.n_lobes, [cam], pitch=sc.pitch)
+    lens = np.diff(oranges)
+    assert lens.max() > 2 * 4096 and ((lens > 512) & (lens <= 1024)).any()
+    assert np.array_equal(ranges, oranges)
+    assert np.array_equal(vals, recs)
+
+
 def test_bin_sort_equal_depth_keys_keep_record_order():
     """Primitives repeated verbatim have equal depth keys in every tile they
     share: the lists hold them in record order, as the oracle's stable sort."""
