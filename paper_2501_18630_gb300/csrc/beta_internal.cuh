@@ -169,7 +169,8 @@ __device__ __forceinline__ bool rule_depth(const PrimGeo& pg, const ViewDev& V, 
 // Rule chain, per-view part after rule_depth: J, M, diagonal of Sigma' and
 // the tile rectangle.  Returns false if the rectangle is empty.
 __device__ __forceinline__ bool rule_view(const PrimGeo& pg, const ViewDev& V, float blur,
-                                          int tile_w, int tile_h, ViewGeo& g, int rect[4]) {
+                                          int tile_shift_w, int tile_shift_h, ViewGeo& g,
+                                          int rect[4]) {
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -213,10 +214,11 @@ __device__ __forceinline__ bool rule_view(const PrimGeo& pg, const ViewDev& V, f
   if (i1 > wm1) i1 = wm1;
   if (j1 > hm1) j1 = hm1;
   if (i0 > i1 || j0 > j1) return false;
-  rect[0] = (int)i0 / tile_w;
-  rect[1] = (int)i1 / tile_w;
-  rect[2] = (int)j0 / tile_h;
-  rect[3] = (int)j1 / tile_h;
+  // pixel index / tile size for power-of-two tiles (indices are >= 0 here)
+  rect[0] = (int)i0 >> tile_shift_w;
+  rect[1] = (int)i1 >> tile_shift_w;
+  rect[2] = (int)j0 >> tile_shift_h;
+  rect[3] = (int)j1 >> tile_shift_h;
   return true;
 }
 

@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(256) k_project(const float* __restrict__ plane
     ViewGeo g;
     int rc[4];
     uint32_t kk = 0xffffffffu;
-    bool bin = ok && rule_depth(pg, V, g, kk) && rule_view(pg, V, ro.blur_eps, ro.tile_w, ro.tile_h, g, rc);
+    bool bin = ok && rule_depth(pg, V, g, kk) &&
+               rule_view(pg, V, ro.blur_eps, __ffs(ro.tile_w) - 1, __ffs(ro.tile_h) - 1, g, rc);
     float4 o0, o1, o2;
     if (bin) {
       // projected centre in double-float
