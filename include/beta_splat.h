@@ -115,8 +115,9 @@ size_t beta_proj_bytes(int32_t pitch, int32_t n_views);
 int64_t beta_total_tiles(const beta_camera* cams /* host */, int32_t n_views, const beta_opts* opt);
 /* Total pixels of a batch of views. */
 int64_t beta_total_pixels(const beta_camera* cams /* host */, int32_t n_views);
-/* Workspace of beta_bin_sort for a pair capacity (radix-sort buffers,
- * look-back tables, scan sums). */
+/* Workspace of beta_bin_sort for a pair capacity (tile counters and list
+ * cursors, the scan's look-back flags, 16 bytes of list items and merge
+ * buffer per pair). */
 size_t beta_binsort_workspace_bytes(int32_t pitch, int32_t n_views, int64_t pair_capacity,
                                     const beta_camera* cams /* host */, const beta_opts* opt);
 /* Workspace of beta_raster_bwd: per-record 2D gradient sums, a 48-byte slot
@@ -135,10 +136,11 @@ int beta_project(const beta_params* prm /* host */, const beta_camera* cams /* h
                  int32_t n_views, const beta_opts* opt /* host */, void* proj,
                  beta_stream_t stream);
 
-/* Step 2 (Sec. 3.2: "sorting overlapping primitives by depth"): emits one
- * (tile, record) pair per tile each record's rectangle touches, sorts the
- * pairs by (global tile, depth key, primitive index) with a project-written
- * onesweep LSD radix sort, and writes the per-tile ranges.
+/* Step 2 (Sec. 3.2: "sorting overlapping primitives by depth"): forms one
+ * (tile, record) pair per tile each record's rectangle touches, as per-tile
+ * lists (atomic counts, their scan, atomic slots), sorts every list by its
+ * unique (depth key, record index) items, and writes the per-tile ranges:
+ * the pairs end up sorted by (global tile, depth key, primitive index).
  *   pair_vals   [pair_capacity] out: record of every sorted pair
  *   tile_ranges [total_tiles + 1] out: pairs of tile g are
  *               pair_vals[tile_ranges[g] .. tile_ranges[g + 1])

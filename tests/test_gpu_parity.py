@@ -51,7 +51,7 @@ def test_project_records_match_oracle(cfg, n, views):
 
 
 # --------------------------------------------------------------------------
-# step 2: binning + radix sort, bit-exact
+# step 2: binning + per-tile list sort, bit-exact
 # --------------------------------------------------------------------------
 
 def _check_bins(sc, cams):
@@ -79,8 +79,9 @@ def test_bin_sort_bit_exact_mixed_view_batch():
 
 @pytest.mark.parametrize("cfg,n_views,tile,bits", [(3, 16, 16, 17), (5, 8, 16, 18), (5, 8, 8, 20)])
 def test_bin_sort_bit_exact_wide_tile_ids(cfg, n_views, tile, bits):
-    """Tile ids of 17-18 bits take two 9-bit passes, wider ones three 8-bit
-    passes: both orderings equal the oracle's bit for bit."""
+    """Many tiles (17-20-bit global tile ids: up to 1M counters and lists,
+    hundreds of scan blocks chained by look-back): lists equal the oracle's
+    bit for bit."""
     sc = scenes.config_scene(cfg, n=20_000, n_views=n_views)
     opts = _lib.default_opts(tile_w=tile, tile_h=tile)
     total = sum(((c.width + tile - 1) // tile) * ((c.height + tile - 1) // tile) for c in sc.cameras)
