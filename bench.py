@@ -371,19 +371,19 @@ def main():
         # ---- end to end through host buffers --------------------------------
         # Every step copies its inputs (parameters, targets) from pinned host
         # memory and reads its results (gradients, losses) back, inside the
-        # timed region.  The copies run on a second stream and are pipelined
-        # with the compute: step i+1's inputs land in a staging buffer while
-        # step i runs, and step i's results leave from a staging buffer while
-        # step i+1 runs.
+        # timed region.  Two captured steps with their own input and output
+        # buffers alternate, so that step i+1's inputs land (copy-in stream)
+        # while step i runs and step i's results leave (copy-out stream) while
+        # step i+1 runs, with no device-side staging copies.
         h_planes = torch.from_numpy(sc.planes).pin_memory()
         h_target = torch.from_numpy(np.concatenate([t.reshape(-1) for t in targets_np])).pin_memory()
         h_grad = torch.empty(planes.shape, dtype=torch.float32).pin_memory()
         h_loss = torch.empty(V, dtype=torch.float32).pin_memory()
-        cstream = torch.cuda.Stream()
-        st_p = [torch.empty_like(planes) for _ in range(2)]
-        st_t = [torch.empty_like(target) for _ in range(2)]
-        st_g = [torch.empty_like(grad) for _ in range(2)]
-        st_l = [torch.empty_like(rast.loss) for _ in range(2)]
+        twin = batched.BatchedStep(torch.empty_like(planes).copy_(planes), sc.n, sc.n_lobes, cams,
+                                   torch.empty_like(target).copy_(target), opts=opts, persistent=persist)
+        twin.capture()
+        steps2 = [bstep, twin]
+        cin, cout = torch.cuda.Stream(), torch.cuda.Stream()
         ev_in = [torch.cuda.Event() for _ in range(2)]
         ev_free = [torch.cuda.Event() for _ in range(2)]
         ev_out = [torch.cuda.Event() for _ in range(2)]
@@ -393,51 +393,52 @@ def main():
 
         def h2d(i):
             b = i % 2
-            with torch.cuda.stream(cstream):
-                cstream.wait_event(ev_free[b])
-                st_p[b].copy_(h_planes, non_blocking=True)
-                st_t[b].copy_(h_target, non_blocking=True)
-                ev_in[b].record(cstream)
+            with torch.cuda.stream(cin):
+                cin.wait_event(ev_free[b])          # the step that last read these inputs is done
+                steps2[b].planes.copy_(h_planes, non_blocking=True)
+                steps2[b].target.copy_(h_target, non_blocking=True)
+                ev_in[b].record(cin)
 
         def step_e2e(i, n):
             b = i % 2
-            stream.wait_event(ev_in[b])
-            planes.copy_(st_p[b])
-            target.copy_(st_t[b])
-            ev_free[b].record(stream)
+            stream.wait_event(ev_in[b])             # inputs landed
+            stream.wait_event(ev_sent[b])           # the previous results of these buffers left
             if i + 1 < n:
                 h2d(i + 1)
-            step()
-            stream.wait_event(ev_sent[b])
-            st_g[b].copy_(grad)
-            st_l[b].copy_(rast.loss)
+            steps2[b].step()
+            ev_free[b].record(stream)
             ev_out[b].record(stream)
-            with torch.cuda.stream(cstream):
-                cstream.wait_event(ev_out[b])
-                h_grad.copy_(st_g[b], non_blocking=True)
-                h_loss.copy_(st_l[b], non_blocking=True)
-                ev_sent[b].record(cstream)
+            with torch.cuda.stream(cout):
+                cout.wait_event(ev_out[b])
+                h_grad.copy_(steps2[b].grad, non_blocking=True)
+                h_loss.copy_(steps2[b].loss, non_blocking=True)
+                ev_sent[b].record(cout)
 
         h2d(0)
         for i in range(args.warmup):
             step_e2e(i, args.warmup)
-        stream.wait_stream(cstream)
+        stream.wait_stream(cin)
+        stream.wait_stream(cout)
         torch.cuda.synchronize()
         barrier()
         e0.record(stream)
         h2d(0)
         for i in range(args.steps):
             step_e2e(i, args.steps)
-        stream.wait_stream(cstream)
+        stream.wait_stream(cout)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
         ms_e2e = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+        st_tw, k_tw = twin.rast.device_status()
+        if st_tw != _lib.BETA_OK:
+            raise _lib.BetaError("e2e step", st_tw, _lib.load().beta_status_string(st_tw).decode())
         extras["e2e"] = {"value": pix_per_step / (ms_e2e * 1e-3) / 1e6, "unit": UNIT,
                          "h2d_bytes_per_step": (h_planes.numel() + h_target.numel()) * 4 * world,
                          "d2h_bytes_per_step": (h_grad.numel() + h_loss.numel()) * 4 * world,
-                         "ms_per_step": ms_e2e, "copies": "pipelined on a second stream"}
-        del st_p, st_t, st_g, st_l
+                         "ms_per_step": ms_e2e,
+                         "copies": "pipelined on copy-in / copy-out streams, two alternating captured steps"}
+        del twin, steps2
 
         # ---- the optimiser step after the backward (Sec. 3.4), HBM-bound ----
         from paper_2501_18630_gb300.optim import BetaAdam

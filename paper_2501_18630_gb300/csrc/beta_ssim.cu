@@ -14,13 +14,12 @@
 //   b = 2 dS/dG*x^2 = -2 S / B2,   c = dS/dG*xy = 2 A1 d
 //   dL/dx = (1 - lambda) sign(x - y) / N - lambda / N (G*a + x G*b + y G*c).
 //
-// k_ssim_stats: one CTA per 32 x 64 pixel tile (wide x tall) of one channel:
-//   x and y over the tile and a 5-pixel halo in shared memory, the
+// k_ssim_stats: one CTA per 32 x 32 pixel tile of one channel: x and y over
+//   the tile and a 5-pixel halo in shared memory, the
 //   horizontal and vertical 11-tap passes with each thread sliding a register
-//   window over 8 outputs (one shared-memory load per input instead of one per
-//   tap; the tall tile keeps the horizontal pass's halo rows to 16%), then S,
-//   (a, b, c) to the workspace and the tile's sums of S and |x - y| as
-//   per-block partials.
+//   window over 4 outputs (one shared-memory load per input instead of one per
+//   tap), then S, (a, b, c) to the workspace and the tile's sums of S and
+//   |x - y| as per-block partials.
 // k_ssim_grad:  the same tiling over (a, b, c): blur them and form dL/dx.
 // k_ssim_loss:  per view, the sum of its blocks' partials (fixed order: the
 //   loss is deterministic) and the loss.
@@ -36,19 +35,16 @@ namespace beta {
 
 namespace {
 
-constexpr int kTX = 32, kTY = 64, kR = 5, kWin = 2 * kR + 1;
-constexpr int kRun = 8;   // outputs per thread in each filter pass (sliding register window)
+constexpr int kTX = 32, kTY = 32, kR = 5, kWin = 2 * kR + 1;
+constexpr int kRun = 4;   // outputs per thread in each filter pass (sliding register window)
 constexpr int kHX = kTX + 2 * kR, kHY = kTY + 2 * kR;
-// row stride of the staged halo tiles: 45, so the eight rows a warp reads in
-// the horizontal pass (4 lanes each, 8 columns apart) fall in 32 distinct banks
+// row stride of the staged halo tiles: 45 = 1 (mod 4), so the four rows a
+// warp reads in the horizontal pass (8 lanes each, 4 columns apart) fall in
+// distinct banks
 constexpr int kSX = 45;
 // row stride of the horizontal-pass results: 33, so the same pass's stores
-// (rows apart by one, 8 columns apart) fall in distinct banks
+// (rows apart by one, 4 columns apart) fall in distinct banks
 constexpr int kSH = kTX + 1;
-static_assert(kTX * (kTY / kRun) == 256, "the vertical pass maps one thread per column run");
-// dynamic shared memory of the two filter kernels (over the 48 KB static limit)
-constexpr size_t kStatsSmem = sizeof(float) * (2 * kHY * kSX + 5 * kHY * kSH);
-constexpr size_t kGradSmem = sizeof(float) * (3 * kHY * kSX + 3 * kHY * kSH);
 constexpr float kC1 = 1e-4f, kC2 = 9e-4f;
 
 // normalised Gaussian taps (sigma 1.5), computed by the host launcher and
@@ -135,9 +131,8 @@ __global__ void __launch_bounds__(256) k_ssim_stats(ViewTable vt, SsimWin win, c
                                                     const float* __restrict__ target,
                                                     float* __restrict__ abc, int64_t plane,
                                                     double* __restrict__ acc) {
-  extern __shared__ float s_dyn[];
-  auto s_in = reinterpret_cast<float (*)[kHY][kSX]>(s_dyn);                     // [2]: x, y and halo
-  auto s_h = reinterpret_cast<float (*)[kHY][kSH]>(s_dyn + 2 * kHY * kSX);     // [5]: horizontal pass
+  __shared__ float s_in[2][kHY][kSX];     // x, y over the tile and its halo
+  __shared__ float s_h[5][kHY][kSH];      // their horizontal pass
   __shared__ double s_w[8];
   const SsimBlock B = ssim_block(vt, blockIdx.x);
   const int64_t HW = (int64_t)B.W * B.H;
@@ -236,9 +231,8 @@ __global__ void __launch_bounds__(256) k_ssim_grad(ViewTable vt, SsimWin win, co
                                                    const float* __restrict__ target,
                                                    const float* __restrict__ abc, int64_t plane, float lambda,
                                                    float* __restrict__ dLdC) {
-  extern __shared__ float s_dyn[];
-  auto s_m = reinterpret_cast<float (*)[kHY][kSX]>(s_dyn);                     // [3]: a, b, c and halo
-  auto s_h = reinterpret_cast<float (*)[kHY][kSH]>(s_dyn + 3 * kHY * kSX);     // [3]: horizontal pass
+  __shared__ float s_m[3][kHY][kSX];
+  __shared__ float s_h[3][kHY][kSH];
   const SsimBlock B = ssim_block(vt, blockIdx.x);
   const int64_t HW = (int64_t)B.W * B.H;
   const int64_t base = 3 * vt.v[B.v].pix_off + B.ch * HW;
@@ -374,17 +368,8 @@ cudaError_t launch_ssim_loss(const ViewTable& vt_in, const float* color, const f
   const int64_t plane = 3 * vt.total_pixels;
   float* abc = (float*)ws;
   double* acc = (double*)((char*)ws + ((size_t)9 * vt.total_pixels * sizeof(float) + 255) / 256 * 256);
-  static bool smem_set = false;
-  if (!smem_set) {
-    if (cudaFuncSetAttribute(k_ssim_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStatsSmem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_ssim_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGradSmem) !=
-            cudaSuccess)
-      return cudaGetLastError();
-    smem_set = true;
-  }
-  k_ssim_stats<<<nb, 256, kStatsSmem, s>>>(vt, win, color, target, abc, plane, acc);
-  k_ssim_grad<<<nb, 256, kGradSmem, s>>>(vt, win, color, target, abc, plane, lambda, dL_dcolor);
+  k_ssim_stats<<<nb, 256, 0, s>>>(vt, win, color, target, abc, plane, acc);
+  k_ssim_grad<<<nb, 256, 0, s>>>(vt, win, color, target, abc, plane, lambda, dL_dcolor);
   k_ssim_loss<<<vt.n_views, 256, 0, s>>>(vt, acc, nb, lambda, loss);
   return cudaGetLastError();
 }
