@@ -14,7 +14,7 @@
  *       C(x) = sum_i c_i o_i B(r_i^2; b_i) prod_{j<i} (1 - o_j B(r_j^2; b_j))  (Sec. 3.2, Eq. C)
  *   - spherical-Beta colour c(V) = c0 + sum_m B(1 - R_m . V; b_m) c_m (Sec. 3.3)
  *
- * Readings where the paper is silent (each one is listed in the design doc):
+ * Readings where the paper is silent:
  *   raw parameters are log-scale, opacity logit and an unnormalised
  *   quaternion (w,x,y,z); the lobe direction is (sin t cos p, sin t sin p,
  *   cos t); the lobe term is 0 when R_m . V <= 0; V = normalize(mu - campos);
@@ -23,8 +23,8 @@
  *   order is the camera-space z of the centre, rounded to fp32 by the rule
  *   below, ties broken by primitive index.
  *
- * Two pieces are not the paper's mathematics but this build's definitions,
- * and both sides implement them from the same written rule:
+ * Two pieces are not the paper's mathematics but fixed rules of this
+ * implementation, and both sides implement them from the same written rule:
  *   (D) the depth key: float bits of tz computed in fp32 as
  *       ((R20*x + R21*y) + R22*z) + t2, every operation rounded;
  *   (B1) the tile rectangle of a primitive, a conservative bound of its
