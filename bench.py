@@ -406,6 +406,7 @@ def main():
             if i + 1 < n:
                 h2d(i + 1)
             steps2[b].step()
+            distributed.reduce_gradients(steps2[b].grad)
             ev_free[b].record(stream)
             ev_out[b].record(stream)
             with torch.cuda.stream(cout):
