@@ -32,7 +32,7 @@ def cache_path() -> str:
 
 def workload_key(n: int, n_lobes: int, cameras, device) -> str:
     res = ",".join(f"{c.width}x{c.height}" for c in cameras)
-    return f"v2;n={n};M={n_lobes};views={res};dev={torch.cuda.get_device_name(device)}"
+    return f"v3;n={n};M={n_lobes};views={res};dev={torch.cuda.get_device_name(device)}"
 
 
 def _load():
