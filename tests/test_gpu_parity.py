@@ -382,21 +382,28 @@ def test_l1_kernel_matches_numpy():
     assert d[5] == 0.0
 
 
-@pytest.mark.parametrize("tile", [(16, 8), (16, 16)])
-def test_forward_with_fused_l1_equals_separate_calls(tile):
-    """beta_raster_fwd_l1 = beta_raster_fwd then beta_l1_loss: the image,
-    T and n_contrib bit for bit, dL/dC bit for bit (the same sign of the same
-    fp32 difference), the per-view loss to fp32 summation order."""
+@pytest.mark.parametrize("tile,persistent", [((16, 8), False), ((16, 16), False), ((16, 8), True)])
+def test_forward_with_fused_l1_equals_separate_calls(tile, persistent):
+    """beta_raster_fwd_l1 = beta_raster_fwd then beta_l1_loss (one CTA per
+    tile, or the persistent longest-first schedule): the image, T and
+    n_contrib bit for bit, dL/dC bit for bit (the same sign of the same fp32
+    difference), the per-view loss to fp32 summation order."""
     sc = scenes.config_scene(4, n=40_000, n_views=8)
     cams = sc.cameras[::2]                                  # four sizes, ragged edge tiles
     opts = _lib.default_opts(tile_w=tile[0], tile_h=tile[1])
-    rast, planes = gc.rasterize(sc.planes, sc.n, sc.n_lobes, cams, opts=opts)
+    gc.ensure_built()
+    planes = torch.from_numpy(np.ascontiguousarray(sc.planes)).cuda()
+    rast = render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, cams, opts, persistent=persistent)
+    rast.forward(planes)
+    torch.cuda.synchronize()
     tgt_np = np.concatenate([t.reshape(-1) for t in scenes.target_images(cams, seed=3)])
     target = torch.from_numpy(tgt_np).cuda()
     rast.raster_fwd(planes)
     loss_a, d_a = (x.clone() for x in rast.l1_loss(target))
     img_a, T_a, n_a = rast.color.clone(), rast.T_final.clone(), rast.n_contrib.clone()
     rast.color.zero_(); rast.T_final.zero_(); rast.dL_dcolor.zero_(); rast.loss.zero_()
+    if persistent:
+        rast.schedule()
     loss_b, d_b = rast.raster_fwd_l1(planes, target)
     torch.cuda.synchronize()
     assert torch.equal(rast.color, img_a) and torch.equal(rast.T_final, T_a)
