@@ -230,9 +230,10 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict_
                                                      float* __restrict__ grad2d,
                                                      float* __restrict__ gout,
                                                      const int32_t* __restrict__ status) {
-  // 2D gradients of views v+1 and v+2 in flight while view v is processed:
+  // 2D gradients of view v+1 in flight while view v is processed (one view
+  // ahead measured faster than two or three):
   // [buffer][float4][thread], each thread reads only its own slots
-  constexpr int kAhead = 2;
+  constexpr int kAhead = 1;
   __shared__ __align__(16) float4 s_g[kAhead + 1][3][256];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
