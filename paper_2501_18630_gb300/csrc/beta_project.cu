@@ -224,8 +224,10 @@ __device__ __forceinline__ void view_geo_bwd(const PrimGeo& pg, const ViewDev& V
 // rotation matrix, the scales and the lobe directions are summed over views
 // first and taken through the view-independent maps once.
 // ---------------------------------------------------------------------------
+constexpr int kBwdThreads = 256, kBwdBlocksPerSM = 2;   // 128 registers a thread
+
 template <int M>
-__global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict__ planes, int n,
+__global__ void __launch_bounds__(kBwdThreads, kBwdBlocksPerSM) k_project_bwd(const float* __restrict__ planes, int n,
                                                      int pitch, ViewTable vt, RenderOpts ro,
                                                      float* __restrict__ grad2d,
                                                      float* __restrict__ gout,
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(256, 2) k_project_bwd(const float* __restrict_
   // ahead measured faster than two or three):
   // [buffer][float4][thread], each thread reads only its own slots
   constexpr int kAhead = 1;
-  __shared__ __align__(16) float4 s_g[kAhead + 1][3][256];
+  __shared__ __align__(16) float4 s_g[kAhead + 1][3][kBwdThreads];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   constexpr int NP = 15 + 6 * M;
@@ -455,9 +457,9 @@ template <int M>
 static cudaError_t launch_project_bwd_m(const float* planes, int n, int pitch, const ViewTable& vt,
                                         const RenderOpts& ro, float* grad2d, float* gout,
                                         const int32_t* status, cudaStream_t s) {
-  int grid = (n + 255) / 256;
+  int grid = (n + kBwdThreads - 1) / kBwdThreads;
   if (grid < 1) return cudaSuccess;
-  k_project_bwd<M><<<grid, 256, 0, s>>>(planes, n, pitch, vt, ro, grad2d, gout, status);
+  k_project_bwd<M><<<grid, kBwdThreads, 0, s>>>(planes, n, pitch, vt, ro, grad2d, gout, status);
   return cudaGetLastError();
 }
 
