@@ -224,7 +224,7 @@ __device__ __forceinline__ void view_geo_bwd(const PrimGeo& pg, const ViewDev& V
 // rotation matrix, the scales and the lobe directions are summed over views
 // first and taken through the view-independent maps once.
 // ---------------------------------------------------------------------------
-constexpr int kBwdThreads = 256, kBwdBlocksPerSM = 2;   // 128 registers a thread
+constexpr int kBwdThreads = 128, kBwdBlocksPerSM = 3;   // up to 170 registers a thread
 
 template <int M>
 __global__ void __launch_bounds__(kBwdThreads, kBwdBlocksPerSM) k_project_bwd(const float* __restrict__ planes, int n,
