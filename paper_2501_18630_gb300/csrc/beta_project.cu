@@ -124,8 +124,10 @@ __device__ __forceinline__ void sb_colour(const float* p, const PrimAttr<M>& a, 
   }
 }
 
+constexpr int kFwdThreads = 256, kFwdBlocksPerSM = 1;
+
 template <int M>
-__global__ void __launch_bounds__(256) k_project(const float* __restrict__ planes, int n, int pitch,
+__global__ void __launch_bounds__(kFwdThreads, kFwdBlocksPerSM) k_project(const float* __restrict__ planes, int n, int pitch,
                                                  ViewTable vt, RenderOpts ro,
                                                  float4* __restrict__ rec, uint2* __restrict__ rect,
                                                  uint32_t* __restrict__ key) {
@@ -447,9 +449,9 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdBlocksPerSM) k_project_bwd(co
 template <int M>
 static cudaError_t launch_project_m(const float* planes, int n, int pitch, const ViewTable& vt,
                                     const RenderOpts& ro, ProjBuffers pb, cudaStream_t s) {
-  int grid = (pitch + 255) / 256;
+  int grid = (pitch + kFwdThreads - 1) / kFwdThreads;
   if (grid < 1) return cudaSuccess;
-  k_project<M><<<grid, 256, 0, s>>>(planes, n, pitch, vt, ro, pb.rec, pb.rect, pb.key);
+  k_project<M><<<grid, kFwdThreads, 0, s>>>(planes, n, pitch, vt, ro, pb.rec, pb.rect, pb.key);
   return cudaGetLastError();
 }
 
