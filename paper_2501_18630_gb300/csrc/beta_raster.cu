@@ -94,6 +94,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const size_t ga = __cvta_generic_to_global(gmem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(ga) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  const size_t ga = __cvta_generic_to_global(gmem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(ga) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -145,6 +150,7 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
   constexpr int NT = TW * TH, BXW = TW / 8, RPT = (S + NT - 1) / NT;
   __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
   __shared__ float s_l1[NT / 32];
+  __shared__ float s_tgt[3][NT];   // the pixel's target, copied in while the tile composites
   __shared__ int s_item;
   if (*status != 0) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -161,6 +167,12 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
     const bool inside = x < W && y < H;
     const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
     const uint32_t start = ranges[g], end = ranges[g + 1];
+    if (target && inside) {
+      const int64_t HW = (int64_t)W * H;
+      const int64_t o = 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) cp_async4(&s_tgt[ch][tid], target + o + ch * HW);
+    }
 
     // batch 0 goes to buffer 0 now; the list entries of batch 1 are loaded
     // ahead so that its copies can be issued without waiting on them
@@ -245,7 +257,7 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
         const float scale = 1.0f / (3.0f * (float)HW);
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
-          const float d = c[ch] - target[o + ch * HW];
+          const float d = c[ch] - s_tgt[ch][tid];   // landed: the copies were waited for above
           l1 += fabsf(d);
           dLdC[o + ch * HW] = d > 0.0f ? scale : (d < 0.0f ? -scale : 0.0f);
         }
