@@ -47,3 +47,39 @@ def test_6m_betas_eight_4k_views_in_budget():
         C, T, _, _ = oracle.render(sc.planes, sc.n, sc.n_lobes, sc.cameras[v], xs, ys)
         img = step.rast.image(step.rast.color, v).cpu().numpy().astype(np.float64)
         assert np.abs(img[:, ys, xs].T - C).max() <= gc.IMG_TOL
+
+
+def test_1m_betas_sixteen_views_benchmark_configuration():
+    """The benchmark's own step: 1M Betas, 16 ring views of 1920x1080, 16x8
+    tiles, 128-record batches, one CTA per tile, captured and replayed.  Two
+    views' binning equals the oracle's bit for bit (a view's lists are the
+    view's own); sampled pixels of two views (including whole tiles) equal
+    the FP64 oracle; the loss and gradients are finite."""
+    from paper_2501_18630_gb300 import _lib
+    sc = scenes.config_scene(3)
+    cams = sc.cameras
+    gc.ensure_built()
+    planes = torch.from_numpy(sc.planes).cuda()
+    tgt = torch.from_numpy(np.concatenate([t.reshape(-1) for t in scenes.target_images(cams, seed=77)])).cuda()
+    step = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, tgt,
+                               opts=_lib.default_opts(tile_w=16, tile_h=8, batch_s=128), persistent=False)
+    step.step()
+    k = step.check()
+    torch.cuda.synchronize()
+    r = step.rast
+    ranges = r.ranges.cpu().numpy().view(np.uint32)
+    vals = r.pair_vals[:k].cpu().numpy().view(np.uint32)
+    for v in (0, 9):
+        _, recs, oranges = oracle.bin_pairs(sc.planes, sc.n, sc.n_lobes, [cams[v]], tile_w=16, tile_h=8,
+                                            pitch=sc.pitch)
+        t0 = sum(int(np.prod(oracle.n_tiles(c, 16, 8))) for c in cams[:v])
+        t1 = t0 + len(oranges) - 1
+        lo = ranges[t0]
+        assert np.array_equal(ranges[t0:t1 + 1] - lo, oranges)
+        assert np.array_equal(vals[lo:ranges[t1]] - v * sc.pitch, recs)
+        xs, ys = scenes.sample_pixels(cams[v], 384, seed=60 + v, full_tiles=1)
+        C, T, _, _ = oracle.render(sc.planes, sc.n, sc.n_lobes, cams[v], xs, ys)
+        img = r.image(r.color, v).cpu().numpy().astype(np.float64)
+        assert np.abs(img[:, ys, xs].T - C).max() <= gc.IMG_TOL
+    assert torch.isfinite(step.loss).all() and torch.isfinite(step.grad).all()
+    assert float(step.grad.abs().max()) > 0.0
