@@ -100,7 +100,7 @@ __device__ __forceinline__ void adam1(float& p, float& m, float& v, float g, flo
 // in flight of a one-primitive thread; a group running past n takes the
 // scalar path so that padding columns are never written.
 template <int M>
-__global__ void __launch_bounds__(256) k_adam(float* __restrict__ planes, const float* __restrict__ grad,
+__global__ void __launch_bounds__(256, 4) k_adam(float* __restrict__ planes, const float* __restrict__ grad,
                                               float* __restrict__ adam_m, float* __restrict__ adam_v,
                                               const float* __restrict__ eta, int n, int pitch, AdamDev a,
                                               double* __restrict__ reg) {
