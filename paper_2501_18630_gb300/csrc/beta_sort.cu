@@ -14,10 +14,12 @@
 //   3. k_tile_scatter: every record appends the 64-bit item
 //                      (depth key << 32 | record) to each of its tiles' lists,
 //                      slots taken with atomics (arbitrary order inside a list);
-//   4. k_tile_sort:    each list is sorted by its items in shared memory (a
-//                      register sorting network per thread, then merge-path
-//                      merges), one warp per list up to kWarpMax items, one
-//                      CTA per longer list, and the record ids are written out.
+//   4. k_tile_sort:    each list is sorted by its items (a register sorting
+//                      network per thread, then a shuffle bitonic network
+//                      across the warp, or merge-path merges in shared memory
+//                      for 16 items a lane and for CTA sorts), one warp per
+//                      list up to kWarpMax items, one CTA per longer list, and
+//                      the record ids are written out.
 // The items of a list are distinct (the record index is part of them), so the
 // sorted list does not depend on the order the atomics gave: it is the order
 // (tile, depth key, record index), a stable sort of the pairs by depth in
