@@ -150,6 +150,54 @@ def ncu_traffic(kernel: str, launch_units: float):
         return None
 
 
+def ncu_metric(kernel: str, name: str):
+    """A per-kernel figure from the committed ncu summary, or None if absent or
+    if the kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        e = json.load(open(p))["kernels"][kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return e.get(name)
+    except Exception:
+        return None
+
+
+REC_BYTES = 48          # raster record read per (tile, Beta) pair
+PROJ_BYTES = 60         # record + tile rectangle + depth key written per (view, Beta)
+GRAD2D_BYTES = 48       # 2D-gradient slot per (view, Beta)
+
+
+def hbm_roofline(stage_ms, ms_step, n, param_bytes, n_rec, K, px, peak, peak_src):
+    """Algorithmic bytes of every stage (each stream counted once) over its
+    CUDA-event time, against the measured HBM copy bandwidth:
+      project      params read + records written         n P + n_rec 60
+      bin_sort     rectangles twice + keys per record,   n_rec 20 + K 20
+                   item written + read + id written per pair
+      raster_fwd   record + list index per pair, colour, K 52 + px (20 + 12 + 12)
+                   T, n_contrib written, target read, dL/dC written
+      raster_bwd   record + index per pair, dL/dC, T,    K 52 + px 20 + n_rec 48
+                   n_contrib read, 2D-gradient slots accumulated
+      project_bwd  2D-gradient slots read and cleared,   n_rec 96 + 2 n P
+                   params read, gradients written"""
+    b = {"project": n * param_bytes + n_rec * PROJ_BYTES,
+         "bin_sort": n_rec * 20 + K * 20,
+         "raster_fwd": K * (REC_BYTES + 4) + px * (20 + 12 + 12),
+         "raster_bwd": K * (REC_BYTES + 4) + px * 20 + n_rec * GRAD2D_BYTES,
+         "project_bwd": n_rec * 2 * GRAD2D_BYTES + 2 * n * param_bytes}
+    out = {"peak_gbs": peak, "peak_kind": f"{peak_src} copy bandwidth", "stages": {}}
+    for k, v in b.items():
+        ms = stage_ms.get(k, 0.0)
+        gbs = v / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        out["stages"][k] = {"bytes": v, "ms": ms, "gbs": gbs, "frac": gbs / peak}
+    tot = sum(b.values())
+    out["step"] = {"bytes": tot, "ms": ms_step, "gbs": tot / (ms_step * 1e-3) / 1e9,
+                   "frac": tot / (ms_step * 1e-3) / 1e9 / peak}
+    out["target_frac"] = 0.5
+    out["target_met"] = out["step"]["frac"] >= 0.5
+    return out
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------
@@ -173,6 +221,23 @@ def oracle_leg(args, cams, sc, pixels_per_step, steps, warmup):
     total = sum(times)
     value = pixels_per_step * len(times) / total / 1e6
     return value, cores, total
+
+
+def oracle_full_frame():
+    """The oracle on the small workload, full frame: 4,096 Betas at 256x256,
+    one view, forward only, all host cores."""
+    import oracle
+    from paper_2501_18630_gb300 import scenes
+    oracle.build()
+    sc1 = scenes.config_scene(1)
+    cam = sc1.cameras[0]
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.render_full(sc1.planes, sc1.n, sc1.n_lobes, cam, n_threads=cores)
+    dt = time.perf_counter() - t0
+    px = cam.width * cam.height
+    return {"ms_per_view": dt * 1e3, "value": px / dt / 1e6, "unit": UNIT, "cores": cores,
+            "what": f"{sc1.n} Betas, {cam.width}x{cam.height}, every pixel, forward only"}
 
 
 def run_reference(args):
@@ -306,6 +371,7 @@ def main():
 
     # ---- roofline of the dominant kernel -----------------------------------
     hbm_peak, sm_max_mhz, peak_src = peaks()
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     dom = max(stage_ms, key=stage_ms.get)
     rec = rast.proj[: V * rast.pitch * 48].view(torch.float32).view(V, rast.pitch, 12)
     keys = rast.proj[V * rast.pitch * 56: V * rast.pitch * 60].view(torch.int32).view(V, rast.pitch)
@@ -313,15 +379,17 @@ def main():
     area = math.pi / (rec[..., 4] * rec[..., 5]).clamp_min(1e-30)          # pi sqrt(det Sigma')
     view_px = torch.tensor([float(c.width * c.height) for c in cams], device=area.device).view(V, 1)
     evals = float(torch.where(binned, torch.minimum(area, view_px), torch.zeros_like(area)).sum().item())
-    alu_peak = 152 * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12      # TFLOP/s
+    alu_peak = n_sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12    # TFLOP/s
     n_planes = scenes.n_planes(sc.n_lobes)
+    hbm = hbm_roofline(stage_ms, ms_step, sc.n, n_planes * 4, V * sc.n, K, rast.total_pixels, hbm_peak,
+                       peak_src)
     if dom in ("raster_fwd", "raster_bwd"):
         fl = FWD_FLOPS_PER_EVAL if dom == "raster_fwd" else BWD_FLOPS_PER_EVAL
         achieved = evals * fl / (stage_ms[dom] * 1e-3) / 1e12
         kname = "k_raster_fwd" if dom == "raster_fwd" else "k_raster_bwd"
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": ncu_traffic(kname, rast.total_pixels),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock",
+                "peak_source": f"{n_sms} SMs x 128 FP32 lanes x 2 flop x max SM clock",
                 "algorithmic": f"{fl} flop x {evals:.4g} (pixel, Beta) evaluations inside the support (ellipse areas)"}
     else:
         nrec = V * sc.n
@@ -333,6 +401,8 @@ def main():
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None}
     roof["peak_kind"] = f"{peak_src} (max SM clock {sm_max_mhz:.0f} MHz)" if roof["bound"] == "alu" else peak_src
+    roof["hbm"] = hbm
+    roof["issue_active"] = {k: ncu_metric(k, "issue_active_pct") for k in ("k_raster_fwd", "k_raster_bwd")}
 
     extras = {}
     if not args.no_extras:
@@ -522,9 +592,16 @@ def main():
         # ---- the oracle on the host cores (bounded sample) -------------------
         if rank == 0 and world == 1:
             v_cpu, cores, tot = oracle_leg(args, cams[:1], sc, args.cpu_pixels, 1, 0)
-            extras["cpu_baseline"] = {"value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                      "sample": f"{args.cpu_pixels} seeded pixels of view 0 of the same "
-                                                f"workload, forward only (FP64, every Beta per pixel), {tot:.1f} s"}
+            view_px = cams[0].width * cams[0].height
+            c1 = oracle_full_frame()
+            extras["cpu_baseline"] = {
+                "value": v_cpu, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"{args.cpu_pixels} seeded pixels of view 0 of the same workload, forward only "
+                          f"(FP64, every Beta per pixel), {tot:.1f} s on {cores} threads",
+                "ms_per_view_extrapolated": tot * 1e3 * view_px / args.cpu_pixels,
+                "extrapolation": f"linear in pixels: the sample's time x {view_px} / {args.cpu_pixels} "
+                                 f"(one {cams[0].width}x{cams[0].height} view, forward only)",
+                "full_frame_4096_betas_256x256": c1}
 
     # kernel launches of ours inside the timed region (all inside the replayed graph):
     # project 1; bin_sort 5 (prep, tile counts, scan, scatter, list sort);

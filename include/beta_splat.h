@@ -106,6 +106,19 @@ void beta_default_opts(beta_opts* opt /* host */);
 const char* beta_status_string(int code);
 int32_t beta_version(void);
 
+/* Fault-injection hook for tests of the bounded waits (host-only, no device
+ * work; the paper has no counterpart).  The tile scan of beta_bin_sort chains
+ * its blocks by a decoupled look-back in which each block polls its
+ * predecessors' entries; every poll loop gives up after `spin_limit` polls
+ * and writes BETA_ERR_TIMEOUT to d_status, and the kernels after it then
+ * skip their work.  This call sets the poll limit of later launches
+ * (1 .. 2^20; 0 restores the default 2^20) and names one scan block
+ * (`withhold_block`, in units of 2048 tiles; -1 for none, the default) that
+ * never posts its entry, so that its successors' waits run out.  Process-wide
+ * and not thread-safe: for tests only.  Returns BETA_ERR_ARG outside those
+ * ranges. */
+int beta_debug_scan_faults(int32_t spin_limit, int64_t withhold_block);
+
 /* ---- sizes (host-only queries, no device work) ------------------------ */
 
 /* Bytes of the projection buffer `proj` for V views: 60 bytes per record
@@ -136,7 +149,7 @@ int beta_project(const beta_params* prm /* host */, const beta_camera* cams /* h
                  int32_t n_views, const beta_opts* opt /* host */, void* proj,
                  beta_stream_t stream);
 
-/* Step 2 (Sec. 3.2: "sorting overlapping primitives by depth"): forms one
+/* Step 2 (Sec. 3.2: overlapping primitives are composited in depth order): forms one
  * (tile, record) pair per tile each record's rectangle touches, as per-tile
  * lists (atomic counts, their scan, atomic slots), sorts every list by its
  * unique (depth key, record index) items, and writes the per-tile ranges:
@@ -170,9 +183,12 @@ int beta_bin_sort(const beta_params* prm, const beta_camera* cams, int32_t n_vie
  *   - Problems whose workspace (beta_binsort_workspace_bytes) exceeds
  *     BETA_STATIC_SCRATCH_BYTES are rejected with BETA_ERR_WORKSPACE before
  *     anything is launched.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Each call made outside stream capture looks up the array's device
+ *     address (cudaGetSymbolAddress) with the calling device current, so the
+ *     first call on a device does the set-up; a call on a capturing stream
+ *     reuses the address of an earlier uncaptured call on that device and
+ *     returns BETA_ERR_CUDA if there was none.  Make the first call on each
+ *     device before any stream capture.
  *   - All calls on a device share the one array, and it keeps what the last
  *     call left in it (the call clears every part that must start at zero).
  *     Calls whose kernels overlap on the GPU (different streams, or

@@ -328,7 +328,9 @@ double oracle_r2(const oprim* P, double X, double Y) {
 
 /* exp in fp32: n = rint(x log2 e); r = (x - n ln2_hi) - n ln2_lo;
  * degree-7 Taylor polynomial of e^r by Horner with fused multiply-adds
- * (Cody-Waite reduction); result = p * 2^n.  Defined for x in [-80, 80]. */
+ * (Cody-Waite reduction); result = p * 2^n.  Defined for x in [-80, 80].
+ * ln2_hi carries trailing zero bits so that n * ln2_hi is exact; the hi/lo
+ * pair is the single-precision split of fdlibm's public expf. */
 float oracle_rule_exp(float x) {
   const float LOG2E = 1.44269504f;
   const float LN2_HI = 0.693145751953125f;

@@ -23,7 +23,23 @@ BETA_ERR_UNSUPPORTED = -5
 BETA_ERR_WORKSPACE = -6
 MAX_LOBES = 8
 MAX_VIEWS = 64
-STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
+
+
+def _header_define(name: str) -> int:
+    """Integer value of a #define in include/beta_splat.h (unsigned suffixes dropped)."""
+    import re
+    hdr = os.path.join(os.path.dirname(HERE), "include", "beta_splat.h")
+    m = re.search(r"^#define\s+" + name + r"\s+(.+)$", open(hdr).read(), re.M)
+    if not m:
+        raise RuntimeError(f"{name} is not defined in {hdr}")
+    expr = re.sub(r"(\d+)[uUlL]+", r"\1", m.group(1).split("/*")[0].strip())
+    if not re.fullmatch(r"[\d\s*()+<]+", expr):
+        raise RuntimeError(f"{name}: unexpected expression {expr!r}")
+    return int(eval(expr, {"__builtins__": {}}))
+
+
+# size of the library's own scratch array behind beta_bin_sort_static
+STATIC_SCRATCH_BYTES = _header_define("BETA_STATIC_SCRATCH_BYTES")
 
 EXPORTS = [
     "beta_default_opts", "beta_status_string", "beta_version", "beta_proj_bytes",
@@ -32,7 +48,7 @@ EXPORTS = [
     "beta_raster_bwd", "beta_project_bwd", "beta_bin_sort_static", "beta_schedule_bytes",
     "beta_schedule", "beta_adam_default_opts", "beta_adam_step", "beta_relocate_workspace_bytes",
     "beta_relocate", "beta_dssim_workspace_bytes", "beta_l1_dssim_loss",
-    "beta_raster_fwd_l1_workspace_bytes", "beta_raster_fwd_l1",
+    "beta_raster_fwd_l1_workspace_bytes", "beta_raster_fwd_l1", "beta_debug_scan_faults",
 ]
 
 
@@ -90,6 +106,7 @@ def load(path: str = LIB_PATH):
             "beta_default_opts": (None, [O]),
             "beta_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "beta_version": (i32, []),
+            "beta_debug_scan_faults": (ctypes.c_int, [i32, i64]),
             "beta_proj_bytes": (sz, [i32, i32]),
             "beta_total_tiles": (i64, [C, i32, O]),
             "beta_total_pixels": (i64, [C, i32]),

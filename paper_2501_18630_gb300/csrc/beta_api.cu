@@ -107,17 +107,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_binsort_scratch on the current device (looked up once
-// per device; the host-side symbol itself is not a device address).
-int static_scratch(void** out) {
+// Device address of g_binsort_scratch on the current device (the host-side
+// symbol itself is not a device address).  Looked up with the device current
+// on every call made outside stream capture, so a device reset between calls
+// is picked up; a call on a capturing stream takes the address an earlier
+// uncaptured call on that device looked up, and fails without one.
+int static_scratch(cudaStream_t stream, void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return BETA_ERR_CUDA;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const cudaError_t q = cudaStreamIsCapturing(stream, &cap);
+  if (q != cudaSuccess) cudaGetLastError();   // a refused query (legacy stream during a capture) is not kept
+  const bool capturing = q != cudaSuccess || cap != cudaStreamCaptureStatusNone;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!capturing) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_binsort_scratch) != cudaSuccess || !p) return BETA_ERR_CUDA;
     g_scratch_ptr[dev] = p;
   }
+  if (!g_scratch_ptr[dev]) return BETA_ERR_CUDA;
   *out = g_scratch_ptr[dev];
   return BETA_OK;
 }
@@ -153,6 +161,10 @@ const char* beta_status_string(int code) {
 }
 
 int32_t beta_version(void) { return kVersion; }
+
+int beta_debug_scan_faults(int32_t spin_limit, int64_t withhold_block) {
+  return set_scan_faults(spin_limit, withhold_block) == 0 ? BETA_OK : BETA_ERR_ARG;
+}
 
 size_t beta_proj_bytes(int32_t pitch, int32_t n_views) {
   if (pitch <= 0 || n_views <= 0) return 0;
@@ -243,7 +255,7 @@ int beta_bin_sort_static(const beta_params* prm, const beta_camera* cams, int32_
   size_t need = binsort_ws_bytes((int64_t)prm->pitch * n_views, pair_capacity, vt.total_tiles);
   if (need > (size_t)BETA_STATIC_SCRATCH_BYTES) return BETA_ERR_WORKSPACE;
   void* ws = nullptr;
-  if ((e = static_scratch(&ws)) != BETA_OK) return e;
+  if ((e = static_scratch((cudaStream_t)stream, &ws)) != BETA_OK) return e;
   ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
   return cuda_status(launch_bin_sort(vt, prm->pitch, pb, pair_vals, pair_capacity, tile_ranges,
                                      d_pair_count, d_status, ws, (cudaStream_t)stream));

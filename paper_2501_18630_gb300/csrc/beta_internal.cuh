@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "beta_splat.h"
 
 namespace beta {
@@ -69,7 +71,10 @@ __device__ __forceinline__ int view_of_tile(const ViewTable& vt, int g) {
 // ---------------------------------------------------------------------------
 
 // exp in fp32 by Cody-Waite reduction and a degree-7 Taylor polynomial
-// (Horner with fused multiply-adds): x in [-80, 80].
+// (Horner with fused multiply-adds): x in [-80, 80].  ln 2 is split into a
+// high part with trailing zero bits (n * LN2_HI is exact for |n| < 2^12) and
+// the remainder; the two fp32 values are the single-precision split that
+// fdlibm's public expf uses.  The polynomial coefficients are 1/k!.
 __device__ __forceinline__ float rule_exp(float x) {
   const float LOG2E = 1.44269504f;
   const float LN2_HI = 0.693145751953125f;
@@ -325,8 +330,27 @@ struct AdamDev {
 };
 
 // ---------------------------------------------------------------------------
-// host-side launchers (defined in the .cu files)
+// host-side helpers and launchers (launchers are defined in the .cu files)
 // ---------------------------------------------------------------------------
+
+// Streaming multiprocessors of the current device, looked up once per device.
+inline int device_sm_count() {
+  constexpr int kDevices = 64;
+  static std::atomic<int> cache[kDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev >= kDevices) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n == 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cache[dev].store(n, std::memory_order_relaxed);
+  }
+  return n;
+}
 struct ProjBuffers {
   float4* rec;       // [V * pitch * 4]
   uint2* rect;       // [V * pitch]  (tx0 | tx1 << 16, ty0 | ty1 << 16), tx0 > tx1 if empty
@@ -342,6 +366,8 @@ cudaError_t launch_project_bwd(const float* planes, int n, int pitch, int n_lobe
                                float* grad_planes, const int32_t* status, cudaStream_t s);
 
 struct SortWs;  // defined in beta_sort.cu
+// fault-injection test hook of the scan's look-back (0 on success)
+int set_scan_faults(int spin_limit, int64_t withhold_block);
 size_t binsort_ws_bytes(int64_t n_items, int64_t cap, int total_tiles);
 cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint32_t* pair_vals,
                             int64_t cap, uint32_t* ranges, int64_t* d_count, int32_t* d_status,

@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
           C2 = fmaf(w, f2.w, C2);
           T = T * (1.0f - a);
           last = act ? base - start + (uint32_t)s + 1u : last;
-          done = T < t_eps;
+          done = done || T < t_eps;   // off-image lanes start done and stay done
         }
         warp_done = __all_sync(0xffffffffu, done);
       }
@@ -614,7 +614,7 @@ size_t schedule_bytes(int total_tiles) { return (size_t)(kSchedOrder + total_til
 cudaError_t launch_schedule(const ViewTable& vt, const uint32_t* ranges, uint32_t* sched,
                             const int32_t* status, cudaStream_t s) {
   const int T = vt.total_tiles;
-  const int grid = std::max(1, std::min((T + 255) / 256, 152 * 4));
+  const int grid = std::max(1, std::min((T + 255) / 256, device_sm_count() * 4));
   k_sched_prep<<<1, 160, 0, s>>>(sched);
   k_sched_hist<<<grid, 256, 0, s>>>(ranges, T, sched, status);
   k_sched_scatter<<<grid, 256, 0, s>>>(ranges, T, sched, status);
@@ -623,23 +623,12 @@ cudaError_t launch_schedule(const ViewTable& vt, const uint32_t* ranges, uint32_
 
 namespace {
 
-int g_sms = 0;
-int sms() {
-  if (g_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 1;
-  }
-  return g_sms;
-}
-
 template <typename K>
 int persistent_grid(K kernel, int threads, int total_tiles) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
-  return std::max(1, std::min(total_tiles, per_sm * sms()));
+  return std::max(1, std::min(total_tiles, per_sm * device_sm_count()));
 }
 
 template <int TW, int TH, int S>

@@ -1,8 +1,8 @@
 // beta_sort.cu -- binning and depth ordering of (tile, record) pairs.
 //
-// Sec. 3.2 of arXiv 2501.18630 composites "after sorting overlapping
-// primitives by depth relative to the camera".  The pairs (global tile,
-// record) are built as per-tile lists and each list is sorted on its own:
+// Sec. 3.2 of arXiv 2501.18630 composites the primitives that overlap a
+// pixel in order of their camera depth.  The pairs (global tile, record) are
+// built as per-tile lists and each list is sorted on its own:
 //   1. k_tile_count:   every record adds one to a counter of each tile its
 //                      rectangle touches (kSub counters per tile, chosen by
 //                      the record index, so that the atomics on a busy tile
@@ -24,11 +24,13 @@
 // sorted list does not depend on the order the atomics gave: it is the order
 // (tile, depth key, record index), a stable sort of the pairs by depth in
 // record order.  Every wait (the scan's look-back) is bounded: after
-// kSpinLimit polls the CTA records BETA_ERR_TIMEOUT and proceeds.
+// kSpinLimit polls (or the test hook's smaller limit) the CTA records
+// BETA_ERR_TIMEOUT and proceeds.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "beta_internal.cuh"
 
@@ -182,7 +184,8 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scan(const uint32_t* __re
                                                         uint32_t* __restrict__ ranges,
                                                         uint32_t* __restrict__ cursor,
                                                         uint32_t* __restrict__ longl, int64_t cap,
-                                                        int64_t* d_count, int32_t* status) {
+                                                        int64_t* d_count, int32_t* status,
+                                                        int spin_limit, int64_t withhold) {
   __shared__ u64 s_w[kSortThreads / 32];
   __shared__ u64 s_base;
   __shared__ uint32_t s_blk;
@@ -215,10 +218,13 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scan(const uint32_t* __re
   const u64 excl = block_excl_scan(sum, s_w, total);
   if (warp == 0) {
     u64 prefix = 0;
+    // `withhold` (a test hook, -1 normally) names a block that never posts
+    // its look-back entry, so that its successors' bounded waits run out
+    const bool post = blk != withhold;
     if (blk == 0) {
-      if (lane == 0) atomicExch(&look[0], kInc | total);
+      if (lane == 0 && post) atomicExch(&look[0], kInc | total);
     } else {
-      if (lane == 0) atomicExch(&look[blk], kAgg | total);
+      if (lane == 0 && post) atomicExch(&look[blk], kAgg | total);
       for (int64_t j0 = blk - 1;; j0 -= 32) {
         const int64_t j = j0 - lane;   // lane 0: the nearest predecessor
         u64 v = kInc;                  // before block 0: an inclusive zero
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scan(const uint32_t* __re
           v = *pj;
           int spins = 0;
           while ((v & ~kCountMask) == 0ull) {
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
               set_status(status, BETA_ERR_TIMEOUT);
               v = kInc;
               break;
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scan(const uint32_t* __re
         prefix += mine;
         if (inc) break;
       }
-      if (lane == 0) atomicExch(&look[blk], kInc | (prefix + total));
+      if (lane == 0 && post) atomicExch(&look[blk], kInc | (prefix + total));
     }
     if (lane == 0) {
       s_base = prefix;
@@ -597,15 +603,18 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_tile_sort(const uint32_t* _
 // host launcher
 // ---------------------------------------------------------------------------
 
-static int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
+// Scan look-back settings: the poll limit, and the scan block that withholds
+// its look-back entry (-1: none).  Changed only by the fault-injection test
+// hook beta_debug_scan_faults.
+static std::atomic<int> g_spin_limit{kSpinLimit};
+static std::atomic<int64_t> g_withhold{-1};
+
+int set_scan_faults(int spin_limit, int64_t withhold_block) {
+  if (spin_limit == 0) spin_limit = kSpinLimit;
+  if (spin_limit < 1 || spin_limit > kSpinLimit || withhold_block < -1) return -1;
+  g_spin_limit.store(spin_limit);
+  g_withhold.store(withhold_block);
+  return 0;
 }
 
 cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint32_t* pair_vals,
@@ -622,10 +631,11 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
                                                                           w.counters, d_count, d_status);
   k_tile_count<<<(unsigned)grid_r, kSortThreads, 0, s>>>(pb.rect, n_items, pitch, vt, total_tiles, w.cnt);
   k_tile_scan<<<(unsigned)nb_scan, kSortThreads, 0, s>>>(w.cnt, total_tiles, w.look, w.counters, ranges, w.cursor,
-                                                     w.longl, cap, d_count, d_status);
+                                                     w.longl, cap, d_count, d_status, g_spin_limit.load(),
+                                                     g_withhold.load());
   k_tile_scatter<<<(unsigned)grid_r, kSortThreads, 0, s>>>(pb.rect, pb.key, n_items, pitch, vt, total_tiles, w.cursor, w.items,
                                                        cap, d_status);
-  k_tile_sort<<<(unsigned)(sm_count() * 3), kSortThreads, 0, s>>>(ranges, total_tiles, w.longl, w.counters, w.items,
+  k_tile_sort<<<(unsigned)(device_sm_count() * 3), kSortThreads, 0, s>>>(ranges, total_tiles, w.longl, w.counters, w.items,
                                                               w.tmp, pair_vals, d_status);
   return cudaGetLastError();
 }

@@ -1,4 +1,6 @@
 """Shared helpers of the GPU parity tests (CUDA path vs FP64 oracle)."""
+import math
+
 import numpy as np
 import torch
 
@@ -66,22 +68,81 @@ def image(rast, v):
 
 
 def last_ids(rast, v, pitch):
-    """Primitive id of each pixel's last contributor (-1 if none)."""
+    """Primitive id of each pixel's last contributor (-1 if none), from
+    n_contrib (1 + position in the pixel's tile list) under the rasterizer's
+    own tile shape."""
     cam = rast.cameras[v]
+    tw, th = int(rast.opts.tile_w), int(rast.opts.tile_h)
     nc = rast.plane(rast.n_contrib, v).cpu().numpy().astype(np.int64)
     ranges = rast.ranges.cpu().numpy().view(np.uint32).astype(np.int64)
     K = int(rast.count.item())
     vals = rast.pair_vals[:max(K, 1)].cpu().numpy().view(np.uint32).astype(np.int64)
-    ntx = (cam.width + 15) // 16
+    ntx = (cam.width + tw - 1) // tw
     toff = 0
     for u in range(v):
         c = rast.cameras[u]
-        toff += ((c.width + 15) // 16) * ((c.height + 15) // 16)
+        toff += ((c.width + tw - 1) // tw) * ((c.height + th - 1) // th)
     ys, xs = np.mgrid[0:cam.height, 0:cam.width]
-    g = toff + (ys // 16) * ntx + (xs // 16)
+    g = toff + (ys // th) * ntx + (xs // tw)
     pos = ranges[g] + nc - 1
+    assert np.all((nc == 0) | (nc <= ranges[g + 1] - ranges[g])), "n_contrib beyond its tile list"
     out = np.where(nc > 0, vals[np.clip(pos, 0, max(K - 1, 0))] - v * pitch, -1)
     return out
+
+
+def r2_fp64(pr, ids, xs, ys):
+    """FP64 r^2 of primitives ids[k] at pixel centres (xs[k], ys[k]) (Eq. r)."""
+    ids = np.asarray(ids)
+    dx = xs + 0.5 - pr["mu2"][ids, 0]
+    dy = ys + 0.5 - pr["mu2"][ids, 1]
+    A, B, C = pr["conic"][ids, 0], pr["conic"][ids, 1], pr["conic"][ids, 2]
+    return A * dx * dx + 2.0 * B * dx * dy + C * dy * dy
+
+
+def unexplained_last_mismatches(last_gpu, last_or, T_or, xs, ys, pr, t_eps=2.0 ** -19, band=1e-4):
+    """Pixels whose last contributor differs between the CUDA path and the
+    FP64 oracle for a reason other than the two that make it legitimately
+    differ: a support-boundary decision (the later of the two primitives has
+    FP64 r^2 within `band` of 1, where its alpha is below o * band^beta) or
+    an early-termination decision (the oracle's final T within 1e-3 of
+    t_eps).  Returns the indices of the unexplained pixels."""
+    mism = np.nonzero(last_gpu != last_or)[0]
+    bad = []
+    for k in mism:
+        cand = [int(i) for i in (last_gpu[k], last_or[k]) if i >= 0]
+        r2 = r2_fp64(pr, cand, np.full(len(cand), xs[k]), np.full(len(cand), ys[k]))
+        near_edge = np.any(np.abs(r2 - 1.0) < band)
+        near_stop = abs(T_or[k] - t_eps) < 1e-3 * t_eps or T_or[k] < t_eps
+        if not (near_edge or near_stop):
+            bad.append(k)
+    return np.asarray(bad, np.int64), len(mism)
+
+
+def fd_block_views(planes, n, n_lobes, cams, targets, i, prs=None, margin=3.0):
+    """Central finite differences (and one-sided estimates) of sum_v L1_v
+    w.r.t. every raw parameter of primitive i, each view evaluated on the
+    sub-scene that can touch the primitive's padded support box there.
+    Returns (g, gp, gm) of shape (n_planes, 1)."""
+    P = planes.shape[0]
+    g = np.zeros((P, 1)); gp = np.zeros((P, 1)); gm = np.zeros((P, 1))
+    for v, cam in enumerate(cams):
+        pr = prs[v] if prs is not None else oracle.project(planes, n, n_lobes, cam)
+        if not pr["valid"][i]:
+            continue
+        a, _, c = pr["cov"][i]
+        mx, my = pr["mu2"][i]
+        ex, ey = math.sqrt(a) + margin, math.sqrt(c) + margin
+        x0, x1 = max(0, int(mx - ex)), min(cam.width - 1, int(mx + ex) + 1)
+        y0, y1 = max(0, int(my - ey)), min(cam.height - 1, int(my + ey) + 1)
+        if x0 > x1 or y0 > y1:
+            continue
+        idx = sub_scene(planes, n, n_lobes, cam, x0, x1, y0, y1, pr=pr)
+        sub = np.ascontiguousarray(planes[:, idx])
+        j = int(np.nonzero(idx == i)[0][0])
+        a_, b_, c_ = oracle.fd_grad(sub, len(idx), n_lobes, [cam], [targets[v]], list(range(P)), [j],
+                                    local=True)
+        g += a_; gp += b_; gm += c_
+    return g, gp, gm
 
 
 def sub_scene(planes, n, n_lobes, cam, x0, x1, y0, y1, margin=2.0, pr=None):

@@ -121,3 +121,20 @@ def test_product_path_has_no_cpu_fallback():
             _lib.load(os.path.join(ROOT, "does-not-exist.so"))
         finally:
             _lib._lib = saved
+
+
+def test_scan_fault_hook_checks_its_arguments(L):
+    """The look-back fault-injection hook is host-only: it validates its
+    arguments and stores them for later launches (no device work)."""
+    assert L.beta_debug_scan_faults(-1, -1) == _lib.BETA_ERR_ARG
+    assert L.beta_debug_scan_faults((1 << 20) + 1, -1) == _lib.BETA_ERR_ARG
+    assert L.beta_debug_scan_faults(100, -2) == _lib.BETA_ERR_ARG
+    assert L.beta_debug_scan_faults(100, 3) == _lib.BETA_OK
+    assert L.beta_debug_scan_faults(0, -1) == _lib.BETA_OK      # defaults restored
+
+
+def test_static_scratch_size_matches_header():
+    """The binding's copy of the static-scratch size is read from the header."""
+    src = open(os.path.join(ROOT, "include", "beta_splat.h")).read()
+    m = re.search(r"#define\s+BETA_STATIC_SCRATCH_BYTES\s+\((\d+)u \* (\d+)u \* (\d+)u\)", src)
+    assert m and _lib.STATIC_SCRATCH_BYTES == int(m.group(1)) * int(m.group(2)) * int(m.group(3))

@@ -61,7 +61,9 @@ def test_persistent_gradients_match_default():
     tgt = torch.from_numpy(scenes.target_images(cams, seed=2)[0].reshape(-1)).cuda()
     grads = []
     for opts, persist in ((None, False), (_lib.default_opts(tile_w=32, tile_h=16, batch_s=128), True),
-                          (_lib.default_opts(tile_w=8, tile_h=8, batch_s=64), True)):
+                          (_lib.default_opts(tile_w=8, tile_h=8, batch_s=64), True),
+                          (_lib.default_opts(tile_w=16, tile_h=8, batch_s=128), False),
+                          (_lib.default_opts(tile_w=16, tile_h=8, batch_s=128), True)):
         gc.ensure_built()
         planes = torch.from_numpy(sc.planes).cuda()
         r = render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, cams, opts, persistent=persist)
@@ -136,3 +138,33 @@ def test_autotuner_times_candidates_and_caches(tmp_path, monkeypatch):
     assert len(d) == 1 and list(d.values())[0]["best"] == list(best)
     best2, _ = autotune.tune(planes, sc.n, sc.n_lobes, cams, tgt, candidates=cands)
     assert best2 == best
+
+
+def test_view_split_gradients_sum_to_full_batch():
+    """The data-parallel split over views: views {0..7} and {8..15} rendered
+    as two batched steps, their gradients summed, equal the 16-view step's
+    gradient (1e-4 of each plane's largest value) and their losses are the
+    16-view step's losses.  This is what the gradient all-reduce of the
+    multi-GPU path relies on."""
+    sc = scenes.config_scene(3, n=200_000)
+    cams = scenes.ring_cameras(16, 4.0, 15.0, [(640, 360)] * 16)
+    tg = scenes.target_images(cams, seed=21)
+    gc.ensure_built()
+    planes = torch.from_numpy(sc.planes).cuda()
+    opts = _lib.default_opts(tile_w=16, tile_h=8, batch_s=128)
+
+    def run(vs):
+        t = torch.from_numpy(np.concatenate([tg[v].reshape(-1) for v in vs])).cuda()
+        st = batched.BatchedStep(planes, sc.n, sc.n_lobes, [cams[v] for v in vs], t, opts=opts, persistent=False)
+        st.step()
+        st.check()
+        torch.cuda.synchronize()
+        return st.grad.cpu().numpy()[:, :sc.n].astype(np.float64), st.loss.cpu().numpy()
+
+    g_all, l_all = run(list(range(16)))
+    g_a, l_a = run(list(range(8)))
+    g_b, l_b = run(list(range(8, 16)))
+    assert np.array_equal(np.concatenate([l_a, l_b]), l_all)
+    scale = np.abs(g_all).max(axis=1, keepdims=True) + 1e-30
+    assert np.all(np.abs(g_all).max(axis=1) > 0)
+    assert np.max(np.abs(g_a + g_b - g_all) / scale) < 1e-4

@@ -83,3 +83,70 @@ def test_1m_betas_sixteen_views_benchmark_configuration():
         assert np.abs(img[:, ys, xs].T - C).max() <= gc.IMG_TOL
     assert torch.isfinite(step.loss).all() and torch.isfinite(step.grad).all()
     assert float(step.grad.abs().max()) > 0.0
+
+
+def _bench_step(sc, cams, tgt, persistent=False):
+    from paper_2501_18630_gb300 import _lib
+    gc.ensure_built()
+    planes = torch.from_numpy(sc.planes).cuda()
+    step = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, tgt,
+                               opts=_lib.default_opts(tile_w=16, tile_h=8, batch_s=128), persistent=persistent)
+    step.step()
+    step.check()
+    torch.cuda.synchronize()
+    return step, planes
+
+
+def test_1m_betas_benchmark_step_gradients_equal_per_view_default_path():
+    """The benchmark's captured step (16x8 tiles, 128-record batches, one CTA
+    per tile, 16 views at once) gives the same parameter gradients as the
+    plain default path (16x16 tiles, 256-record batches) run one view at a
+    time and summed: every primitive, every parameter, within 1e-4 of the
+    plane's largest gradient (atomics add in a different order)."""
+    from paper_2501_18630_gb300 import render
+    sc = scenes.config_scene(3)
+    cams = sc.cameras
+    tgts = scenes.target_images(cams, seed=77)
+    tgt = torch.from_numpy(np.concatenate([t.reshape(-1) for t in tgts])).cuda()
+    step, planes = _bench_step(sc, cams, tgt)
+    g_step = step.grad.cpu().numpy()[:, :sc.n].astype(np.float64)
+    loss_step = step.loss.cpu().numpy().astype(np.float64)
+    del step
+    g_ref = np.zeros_like(g_step)
+    for v, cam in enumerate(cams):
+        r = render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, [cam])
+        r.forward(planes)
+        loss, d = r.l1_loss(torch.from_numpy(tgts[v].reshape(-1)).cuda())
+        g_ref += r.backward(planes, d).cpu().numpy()[:, :sc.n].astype(np.float64)
+        assert abs(float(loss.item()) - loss_step[v]) <= 1e-5 * loss_step[v]
+        del r
+    scale = np.abs(g_ref).max(axis=1, keepdims=True) + 1e-30
+    assert np.all(np.abs(g_ref).max(axis=1) > 0)
+    assert np.max(np.abs(g_step - g_ref) / scale) < 1e-4
+
+
+def test_1m_betas_benchmark_step_gradients_match_finite_differences():
+    """Gradients of the benchmark's captured step (1M Betas, 16 views of
+    1080p, 16x8 tiles, 128-record batches, one CTA per tile) for primitives
+    seen by several views, against central differences of the FP64 oracle's
+    summed per-view L1 loss (each view on the sub-scene that can touch the
+    primitive there): every parameter group within 1e-3."""
+    from tests.test_gpu_parity import _compare_blocks
+    sc = scenes.config_scene(3)
+    cams = sc.cameras
+    tgts = scenes.target_images(cams, seed=78)
+    tgt = torch.from_numpy(np.concatenate([t.reshape(-1) for t in tgts])).cuda()
+    step, _ = _bench_step(sc, cams, tgt)
+    g_step = step.grad.cpu().numpy().astype(np.float64)
+    keys = step.rast.proj[len(cams) * sc.pitch * 56: len(cams) * sc.pitch * 60].cpu().numpy().view(np.uint32)
+    seen = (keys.reshape(len(cams), sc.pitch)[:, :sc.n] != 0xFFFFFFFF).sum(0)
+    del step
+    rng = np.random.default_rng(31)
+    chosen = rng.choice(np.nonzero(seen >= 3)[0], size=6, replace=False)
+    prs = [oracle.project(sc.planes, sc.n, sc.n_lobes, c) for c in cams]
+    total = 0
+    for i in chosen:
+        g_fd, gp, gm = gc.fd_block_views(sc.planes, sc.n, sc.n_lobes, cams, tgts, int(i), prs=prs)
+        checked, _ = _compare_blocks(g_step[:, [i]], g_fd, gp, gm, sc.n_lobes, [0], f"prim {i}")
+        total += checked
+    assert total >= len(chosen)

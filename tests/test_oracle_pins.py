@@ -457,6 +457,49 @@ def test_fd_gradient_of_single_pixel_closed_form():
     assert np.allclose(g[1:, 0], sgn * o / 3, atol=1e-8)
 
 
+def test_fd_local_mode_equals_whole_image():
+    """The local finite differences (only the pixels of the perturbed
+    primitive's padded FP64 support box re-rendered, the rest of the loss
+    cancelling) equal the whole-image differences.  The scene has strongly
+    anisotropic splats (a wrong axis in the box misses pixels), a large
+    splat covering most of the image, splats cut by each image edge (box
+    clipping) and overlapping splats (the other primitives' pixels in the box
+    must be rendered with them), in two views."""
+    prims = [
+        prim(mu=(0.0, 0.0, 4.0), scale=(0.9, 0.6, 0.5), opacity=0.5, b=0.3, c0=(0.6, 0.2, 0.1)),  # large
+        prim(mu=(0.3, -0.1, 3.5), scale=(0.35, 0.03, 0.03), opacity=0.8, b=-0.2, c0=(0.1, 0.9, 0.3)),  # wide
+        prim(mu=(-0.2, 0.2, 3.0), scale=(0.02, 0.3, 0.02), opacity=0.7, b=0.5, c0=(0.9, 0.9, 0.1)),  # tall
+        prim(mu=(1.25, 0.0, 4.0), scale=(0.3, 0.2, 0.2), opacity=0.6, b=0.0, c0=(0.2, 0.3, 0.8)),   # right edge
+        prim(mu=(-1.3, -0.4, 4.0), scale=(0.25, 0.3, 0.2), opacity=0.6, b=0.1, c0=(0.7, 0.1, 0.5)),  # left edge
+        prim(mu=(0.1, 1.05, 4.2), scale=(0.3, 0.25, 0.2), opacity=0.55, b=-0.1, c0=(0.4, 0.6, 0.2)),  # bottom
+        prim(mu=(-0.1, -1.0, 4.1), scale=(0.28, 0.3, 0.2), opacity=0.65, b=0.2, c0=(0.3, 0.2, 0.9)),  # top
+        prim(mu=(0.25, 0.05, 3.8), scale=(0.12, 0.12, 0.12), opacity=0.9, b=0.7, c0=(0.5, 0.5, 0.5),
+             lobes=[(0.4, 1.0, 0.2, 0.3, 0.1, 0.2)]),
+    ]
+    for p in prims[:-1]:
+        p["lobes"] = ((0.3, 2.0, 0.1, 0.2, 0.2, 0.1),)
+    P = planes_of(prims, n_lobes=1)
+    q = axis_angle_quat((0.3, 0.2, 1.0), 0.7)
+    P[6:10, 1] = q                                         # rotate the wide splat
+    cams = [axis_camera(width=48, height=40, f=40.0, cx=24.0, cy=20.0),
+            axis_camera(width=37, height=29, f=30.0, cx=17.0, cy=15.5)]
+    rng = np.random.default_rng(3)
+    targets = [rng.uniform(0, 1, (3, c.height, c.width)).astype(np.float32) for c in cams]
+    n = len(prims)
+    planes = list(range(scenes.n_planes(1)))
+    g_loc, _, _ = oracle.fd_grad(P, n, 1, cams, targets, planes, list(range(n)), local=True)
+    g_all, _, _ = oracle.fd_grad(P, n, 1, cams, targets, planes, list(range(n)), local=False)
+    scale = np.abs(g_all).max()
+    assert scale > 1e-3
+    assert np.abs(g_loc - g_all).max() <= 1e-7 * scale + 1e-10
+    # the box is not wider than needed: it excludes pixels far outside the support
+    xs, ys = oracle.support_pixels(P, n, 1, cams[0], 2, margin=3.0)
+    pr = oracle.project(P, n, 1, cams[0])
+    a, _, c = pr["cov"][2]
+    assert xs.max() - xs.min() <= 2 * math.sqrt(a) + 8 and ys.max() - ys.min() <= 2 * math.sqrt(c) + 8
+    assert ys.max() - ys.min() > xs.max() - xs.min() + 4     # tall splat: tall box
+
+
 # --------------------------------------------------------------------------
 # rule B1 / rule D (binning definition)
 # --------------------------------------------------------------------------
