@@ -9,18 +9,25 @@
 //
 // Layout: one CTA per TW x TH tile, one pixel per thread; warp w owns an 8x4
 // pixel block.  Records of the tile's list are staged S at a time in shared
-// memory (double-buffered cp.async, one batch ahead); each warp tests 32
-// staged records at a time against its block (an exact ellipse-vs-rectangle
-// test, one record per lane) and walks only the hits (ballot), so whole warps
-// skip records that cannot touch them.  Transmittance early exit is decided
-// per warp (__all_sync) and per CTA (__syncthreads_or).
+// memory (double-buffered cp.async, one batch ahead).  Each warp walks the
+// staged records 32 at a time in two passes.  First, lane k works out which
+// of the block's 32 pixel centres record k may cover (per pixel row the
+// support is an interval in x, solved in closed form and widened slightly),
+// and a 32 x 32 bit transpose across the warp turns these into, per lane, the
+// set of records that may cover its own pixel.  Then every lane composites (or
+// differentiates) only its own records, in list order, after the exact r^2
+// test: the warp iterates as often as its busiest lane rather than once per
+// record touching the block (small Betas cover ~7 of a block's 32 pixels).
+// Transmittance early exit is decided per warp (__all_sync) and per CTA
+// (__syncthreads_or).
 //
 // Backward: the same tiling walks each tile list from the largest
 // last-contributor position down, recovering T_k = T_{k+1} / (1 - alpha_k)
 // and the suffix colour S (as g . S), and produces per-record 2D gradients
-// (d mu', d Sigma', d o, d beta, d colour): up to 12 active lanes add their
-// ten values with three 16-byte vector atomics each, otherwise the warp sums
-// them with a 12-shuffle reduce-scatter and issues one atomic per value.
+// (d mu', d Sigma', d o, d beta, d colour): every lane adds its ten values
+// with three 16-byte vector atomics, except for records covering more than
+// 12 of the block's lanes, which the warp processes together and sums with a
+// 12-shuffle reduce-scatter, one atomic per value.
 //
 // Scheduling: with a schedule buffer (beta_schedule) the raster kernels are
 // persistent -- a grid sized to the SMs takes tiles from a global counter in
@@ -50,41 +57,72 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Does the support r^2 < 1 of a record reach a pixel centre of the 8x4 block
-// whose first pixel is (bxf, byf)?  Conservative by a 1% margin on r^2: the
-// test is the minimum of the convex r^2 over the block's rectangle of pixel
-// centres, in closed form and without divisions.  With A = p^2 + q2^2:
-//   support box:    |dx| <= 1/p,  |dy| <= sqrt(A) / (p q1);
-//   vertical edge:  r^2(x, y) = (p x)^2 + (q2 x + q1 y)^2, and q2 x + q1 y is
-//                   increasing in y, so its square is least at the end
-//                   nearest zero (or zero between the ends);
-//   horizontal edge y: the interior minimum over x is (p q1 y)^2 / A, taken
-//                   when d/dx = 2 (A x + q1 q2 y) changes sign on the edge
-//                   (else the minimum is a corner, covered by the vertical edges).
-__device__ __forceinline__ bool block_hit(float4 f0, float4 f1, float bxf, float byf) {
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Pixels of the 8x4 block with first pixel (bxf, byf) whose centre the
+// record's support r^2 < 1 may cover: bit 8 r + j for row r, column j.  On a
+// row, r^2 = (p dx)^2 + (q2 dx + q1 dy)^2 is a convex quadratic in dx, so its
+// support is the interval dx in [xc - w, xc + w] with A = p^2 + q2^2,
+// xc = -q1 q2 dy / A and w = sqrt(A - (p q1 dy)^2) / A (empty when the root
+// is imaginary).  It is solved for r^2 < 1 + 1e-5 and widened by 1e-3 pixel
+// plus 1e-5 of its extent, so every pixel the exact fp32 test of rec_r2
+// accepts is covered (the compositing repeats that test); dy is formed as
+// rec_r2 forms it.
+__device__ __forceinline__ uint32_t block_cover(float4 f0, float4 f1, float bxf, float byf) {
   const float p = f1.x, q1 = f1.y, q2 = f1.z;
-  const float x0 = (bxf - f0.x) + f0.z, x1 = x0 + 7.0f;
-  const float y0 = (byf - f0.y) + f0.w, y1 = y0 + 3.0f;
-  const float m = 1.01f;
-  const float A = fmaf(p, p, q2 * q2), pq = p * q1;
-  const float xn = x1 < 0.0f ? x1 : (x0 > 0.0f ? x0 : 0.0f);   // block point nearest the centre
-  const float yn = y1 < 0.0f ? y1 : (y0 > 0.0f ? y0 : 0.0f);
-  const float ux = p * xn, uy = pq * yn;
-  if (ux * ux > m || uy * uy > m * A) return false;              // outside the support box
-  if (xn == 0.0f && yn == 0.0f) return true;                     // centre inside the block
-  float best = 3.0e38f;
+  const float X0 = (bxf - f0.x) + f0.z;              // dx of the block's first column
+  const float A = fmaf(p, p, q2 * q2);
+  const float iA = rcp_approx(A);
+  const float A1 = A * 1.00001f;
+  const float sxc = q1 * q2 * iA;
+  const float pq = p * q1;
+  uint32_t m = 0u;
 #pragma unroll
-  for (int e = 0; e < 2; ++e) {
-    const float xc = e ? x1 : x0;
-    const float w0 = fmaf(q2, xc, q1 * y0), w1 = fmaf(q2, xc, q1 * y1);
-    const float wm = w0 > 0.0f ? w0 : (w1 < 0.0f ? w1 : 0.0f);
-    const float u = p * xc;
-    best = fminf(best, fmaf(u, u, wm * wm));
-    const float yc = e ? y1 : y0;
-    const float B = q1 * q2 * yc, uc = pq * yc;
-    if (fmaf(A, x0, B) < 0.0f && fmaf(A, x1, B) > 0.0f && uc * uc < m * A) best = 0.0f;
+  for (int r = 0; r < 4; ++r) {
+    const float dy = ((byf + (float)r) - f0.y) + f0.w;
+    const float t = pq * dy;
+    const float disc = fmaf(-t, t, A1);
+    const float w = sqrt_approx(fmaxf(disc, 0.0f)) * iA;
+    const float xc = fmaf(-sxc, dy, -X0);              // interval centre, in columns of the block
+    const float e = fmaf(1e-5f, fabsf(xc) + w, 1e-3f);
+    const int ilo = (int)fminf(fmaxf(ceilf(xc - w - e), 0.0f), 8.0f);
+    const int ihi = (int)fmaxf(fminf(floorf(xc + w + e), 7.0f), -1.0f);
+    const uint32_t row = (0xFFu >> (7 - ihi)) & (0xFFu << ilo);   // columns ilo .. ihi
+    m |= (disc > 0.0f ? row : 0u) << (8 * r);
   }
-  return best < m;
+  return m;
+}
+
+// 32 x 32 bit-matrix transpose across the warp: on entry lane L holds row L,
+// on return lane j holds column j (bit L of lane j's word = bit j of lane L's).
+// Five exchange stages; at stage s lanes L and L ^ s swap the off-diagonal
+// s x s blocks of their 2s x 2s block.
+__device__ __forceinline__ uint32_t transpose32(uint32_t w, int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
+                     : s == 2 ? 0x33333333u : 0x55555555u;
+    const bool up = (lane & s) != 0;
+    const uint32_t send = up ? (w & m) << s : (w & ~m) >> s;
+    const uint32_t got = __shfl_xor_sync(0xffffffffu, send, s);
+    w = (w & (up ? ~m : m)) | got;
+  }
+  return w;
+}
+
+// r^2 of a staged record at the pixel centre (xf, yf), with the whitened
+// coordinates u, v.  One expression for every caller, so that the support
+// test of the first pass and the compositing of the second see the same value.
+__device__ __forceinline__ float rec_r2(float4 f0, float4 f1, float xf, float yf, float& u, float& vv) {
+  const float dx = (xf - f0.x) + f0.z;
+  const float dy = (yf - f0.y) + f0.w;
+  u = f1.x * dx;
+  vv = fmaf(f1.z, dx, f1.y * dy);
+  return fmaf(u, u, vv * vv);
 }
 
 // Asynchronous 16-byte global -> shared copies (LDGSTS), so record staging
@@ -208,34 +246,38 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
       cp_async_commit();
       const int cnt = (int)min((uint32_t)S, end - base);
       for (int c = 0; c < cnt && !warp_done; c += 32) {
-        // lane k tests record c + k against this warp's block
+        // pass 1: lane k finds the pixels of this warp's block that record
+        // c + k may cover; the transpose gives every lane the records that
+        // may cover its own pixel
         const int idx = c + lane;
-        const bool bit = idx < cnt && block_hit(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf);
-        uint32_t bits = __ballot_sync(0xffffffffu, bit);
-        while (bits) {
-          const int k = __ffs(bits) - 1;
-          bits &= bits - 1;
+        const uint32_t cov = idx < cnt ? block_cover(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
+        uint32_t mine = transpose32(cov, lane);
+        if (done) mine = 0u;   // off-image lanes start done and stay done
+        // pass 2: every lane composites its own hits in list order, so the
+        // warp iterates as often as its busiest lane, not once per record
+        // that touches the block
+        while (mine) {
+          const int k = __ffs(mine) - 1;
+          mine &= mine - 1;
           const int s = c + k;
           const float4 f0 = s_rec[buf][s][0];
           const float4 f1 = s_rec[buf][s][1];
-          const float dx = (xf - f0.x) + f0.z;
-          const float dy = (yf - f0.y) + f0.w;
-          const float u = f1.x * dx;
-          const float vv = fmaf(f1.z, dx, f1.y * dy);
-          const float r2 = fmaf(u, u, vv * vv);
-          // evaluated by every lane (no divergent branch); lanes outside the
-          // support or already done add nothing (their garbage is selected away)
-          const bool act = !done && r2 < 1.0f;
+          float u, vv;
+          const float r2 = rec_r2(f0, f1, xf, yf, u, vv);
+          if (!(r2 < 1.0f)) continue;                  // outside the support (the cover is conservative)
           const float4 f2 = s_rec[buf][s][2];
           const float lb = lg2_approx(1.0f - r2);
-          const float a = act ? fminf(ex2_approx(fmaf(f1.w, lb, f2.x)), amax) : 0.0f;
+          const float a = fminf(ex2_approx(fmaf(f1.w, lb, f2.x)), amax);
           const float w = a * T;
           C0 = fmaf(w, f2.y, C0);
           C1 = fmaf(w, f2.z, C1);
           C2 = fmaf(w, f2.w, C2);
           T = T * (1.0f - a);
-          last = act ? base - start + (uint32_t)s + 1u : last;
-          done = done || T < t_eps;   // off-image lanes start done and stay done
+          last = base - start + (uint32_t)s + 1u;
+          if (T < t_eps) {
+            done = true;
+            mine = 0u;
+          }
         }
         warp_done = __all_sync(0xffffffffu, done);
       }
@@ -326,6 +368,52 @@ __device__ __forceinline__ int warp_sum10_field(int lane) {
     sub = b3 ? (b2 ? 4 : 3) : 2;
   }
   return (b4 ? 5 : 0) + sub;
+}
+
+// Records covering more lanes than this are reduced across the warp before
+// their atomics; the others' lanes add their own terms (measured sweep of the
+// threshold: 8 / 12 / 16 / 20 lanes gave 4.01 / 3.80 / 3.83 / 4.03 ms).
+constexpr int kLaneAtomics = 12;
+
+// Per-lane terms of a record's 2D gradients at this lane's pixel, in whitened
+// coordinates (u, v) = L^-1 (x - mu'); beta, 1/o, ln 2 and the whitening
+// matrix are per-record constants applied by the projection backward:
+//   G0..G4 = k (u, v, u^2, u v, v^2),  k = (dL/dalpha) alpha / (1 - r^2)
+//   G5 = (dL/dalpha) alpha,  G6 = G5 log2(1 - r^2),  G7..9 = alpha T dL/dC.
+// The forward's alpha is recomputed; T_k = T_{k+1} / (1 - alpha_k) and the
+// suffix colour GS (as g . S) are updated only where `act` holds and the
+// pixel lies inside the support (r^2 < 1); returns that condition.
+__device__ __forceinline__ bool bwd_terms(float4 f0, float4 f1, float4 f2, float xf, float yf, float amax,
+                                          bool act, float gx, float gy, float gz, float& T, float& GS,
+                                          float G[kGrad2d]) {
+  float u, vv;
+  const float r2 = rec_r2(f0, f1, xf, yf, u, vv);
+  act = act && r2 < 1.0f;
+  const float beta = f1.w;
+  const float base = 1.0f - r2;
+  const float lb = lg2_approx(base);
+  const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
+  const float a = fminf(a0, amax);
+  const float inv = rcp_approx(1.0f - a);
+  const float Tk = T * inv;
+  const float gc = fmaf(gx, f2.y, fmaf(gy, f2.z, gz * f2.w));
+  const float dLa = fmaf(Tk, gc, -GS * inv);
+  const float wgt = a * Tk;
+  G[7] = wgt * gx;
+  G[8] = wgt * gy;
+  G[9] = wgt * gz;
+  const float t = a0 < amax ? dLa * a0 : 0.0f;           // clamped alpha: no o/beta/r^2 gradient
+  const float kk = t * rcp_approx(base);
+  G[0] = kk * u;
+  G[1] = kk * vv;
+  G[2] = G[0] * u;
+  G[3] = G[0] * vv;
+  G[4] = G[1] * vv;
+  G[5] = t;
+  G[6] = t * lb;
+  GS = act ? fmaf(wgt, gc, GS) : GS;
+  T = act ? Tk : T;
+  return act;
 }
 
 template <int TW, int TH, int S, bool PERSIST>
@@ -423,74 +511,52 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
       }
       for (int c = ((cnt - 1) >> 5) << 5; c >= 0; c -= 32) {
         if ((uint32_t)(lo + c) >= wmax) continue;
-        // lane k tests record c + k against this warp's block
+        // pass 1: lane k finds the pixels of this warp's block that record
+        // c + k may cover (records at or past the warp's last contributor
+        // are skipped); records covering more than kLaneAtomics pixels are
+        // marked `wide`; the transpose gives every lane its own records
         const int idx = c + lane;
-        const bool bit = idx < cnt && (uint32_t)(lo + idx) < wmax &&
-                         block_hit(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf);
-        uint32_t bits = __ballot_sync(0xffffffffu, bit);
-        while (bits) {
-          const int k = 31 - __clz(bits);
-          bits &= ~(1u << k);
-          const int s = c + k;
-          const uint32_t pos = (uint32_t)(lo + s);
-          const float4 f0 = s_rec[buf][s][0];
-          const float4 f1 = s_rec[buf][s][1];
-          const float dx = (xf - f0.x) + f0.z;
-          const float dy = (yf - f0.y) + f0.w;
-          const float u = f1.x * dx;
-          const float vv = fmaf(f1.z, dx, f1.y * dy);
-          const float r2 = fmaf(u, u, vv * vv);
-          const bool act = pos < nl && r2 < 1.0f;
-          const uint32_t amask = __ballot_sync(0xffffffffu, act);
-          if (amask == 0u) continue;
-          // Per-lane terms of the record's 2D gradients, in whitened coordinates
-          // (u, v) = L^-1 (x - mu'); beta, 1/o, ln 2 and the whitening matrix are
-          // per-record constants applied by the projection backward:
-          //   G0..G4 = k (u, v, u^2, u v, v^2),  k = (dL/dalpha) alpha / (1 - r^2)
-          //   G5 = (dL/dalpha) alpha,  G6 = G5 log2(1 - r^2),  G7..9 = alpha T dL/dC
-          // evaluated by every lane (no divergent branch); only active lanes
-          // update their state and add their values
-          float G[kGrad2d];
-          const float4 f2 = s_rec[buf][s][2];
-          const float beta = f1.w;
-          const float base = 1.0f - r2;
-          const float lb = lg2_approx(base);
-          const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
-          const float a = fminf(a0, amax);
-          const float inv = rcp_approx(1.0f - a);
-          const float Tk = T * inv;
-          const float gc = fmaf(gx, f2.y, fmaf(gy, f2.z, gz * f2.w));
-          const float dLa = fmaf(Tk, gc, -GS * inv);
-          const float wgt = a * Tk;
-          G[7] = wgt * gx;
-          G[8] = wgt * gy;
-          G[9] = wgt * gz;
-          const float t = a0 < amax ? dLa * a0 : 0.0f;           // clamped alpha: no o/beta/r^2 gradient
-          const float kk = t * rcp_approx(base);
-          G[0] = kk * u;
-          G[1] = kk * vv;
-          G[2] = G[0] * u;
-          G[3] = G[0] * vv;
-          G[4] = G[1] * vv;
-          G[5] = t;
-          G[6] = t * lb;
-          GS = act ? fmaf(wgt, gc, GS) : GS;
-          T = act ? Tk : T;
-          float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
-          if (__popc(amask) <= 12) {
-            // up to 12 lanes: each adds its ten values with three vector atomics,
-            // cheaper than the cross-lane reduction
-            if (act) {
-              red_add_v4(gdst + 0, G[0], G[1], G[2], G[3]);
-              red_add_v4(gdst + 4, G[4], G[5], G[6], G[7]);
-              red_add_v4(gdst + 8, G[8], G[9], 0.0f, 0.0f);
-            }
-          } else {
-#pragma unroll
-            for (int q = 0; q < kGrad2d; ++q) G[q] = act ? G[q] : 0.0f;
-            const float tot = warp_sum10(G, lane);
-            if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
+        const uint32_t cov = (idx < cnt && (uint32_t)(lo + idx) < wmax)
+                                 ? block_cover(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
+        uint32_t wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
+        uint32_t mine = transpose32(cov, lane);
+        const int lim = (int)nl - (lo + c);            // only positions before this pixel's last contributor
+        mine &= lim >= 32 ? 0xffffffffu : (lim <= 0 ? 0u : (1u << lim) - 1u);
+        // pass 2, in reverse list order: between wide records every lane walks
+        // its own hits and adds its terms with three vector atomics; a wide
+        // record is done by the whole warp together (reduce-scatter, one
+        // atomic per value)
+        for (;;) {
+          const int kb = wide ? 31 - __clz(wide) : -1;                 // warp-uniform
+          const uint32_t above = kb >= 0 ? ~((2u << kb) - 1u) : 0xffffffffu;
+          uint32_t seg = mine & above;
+          mine &= ~above;
+          while (seg) {
+            const int k = 31 - __clz(seg);
+            seg &= ~(1u << k);
+            const int s = c + k;
+            float G[kGrad2d];
+            if (!bwd_terms(s_rec[buf][s][0], s_rec[buf][s][1], s_rec[buf][s][2], xf, yf, amax, true, gx, gy, gz,
+                           T, GS, G))
+              continue;                                // outside the support (the cover is conservative)
+            float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
+            red_add_v4(gdst + 0, G[0], G[1], G[2], G[3]);
+            red_add_v4(gdst + 4, G[4], G[5], G[6], G[7]);
+            red_add_v4(gdst + 8, G[8], G[9], 0.0f, 0.0f);
           }
+          if (kb < 0) break;
+          wide &= ~(1u << kb);
+          const bool mine_kb = (mine >> kb) & 1u;
+          mine &= ~(1u << kb);
+          const int s = c + kb;
+          float G[kGrad2d];
+          const bool act = bwd_terms(s_rec[buf][s][0], s_rec[buf][s][1], s_rec[buf][s][2], xf, yf, amax, mine_kb,
+                                     gx, gy, gz, T, GS, G);
+#pragma unroll
+          for (int q = 0; q < kGrad2d; ++q) G[q] = act ? G[q] : 0.0f;
+          const float tot = warp_sum10(G, lane);
+          float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
+          if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
         }
       }
       buf ^= 1;
