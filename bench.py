@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-pixels", type=int, default=16384)
     ap.add_argument("--workload", type=int, default=3, choices=[3, 4, 5],
                     help="scene recipe: 3 = 1M Betas (default), 4 = 3M Betas, 5 = 6M Betas")
+    ap.add_argument("--no-hit-masks", action="store_true",
+                    help="the raster backward recomputes its cover pass instead of reading the forward's")
     ap.add_argument("--config", default=None,
                     help="pin the raster configuration instead of autotuning, e.g. 16x16/256/P (P persistent, G one CTA per tile)")
     return ap.parse_args()
@@ -301,18 +303,22 @@ def main():
 
     # ---- autotuned batched step, captured as one CUDA graph -----------------
     from paper_2501_18630_gb300 import autotune, batched
+    # the 6M-Beta 4K workload keeps no per-pixel state between the raster
+    # passes beyond T and n_contrib (its backward recomputes the cover pass)
+    hit_masks = args.workload != 5 and not args.no_hit_masks
     t_tune = time.perf_counter()
     if args.config:
         shape, bsz, mode = args.config.split("/")
         tw_, th_ = (int(x) for x in shape.split("x"))
         best, tune_ms = (tw_, th_, int(bsz), mode.upper() == "P"), {}
     else:
-        best, tune_ms = autotune.tune(planes, sc.n, sc.n_lobes, cams, target, reps=3,
+        best, tune_ms = autotune.tune(planes, sc.n, sc.n_lobes, cams, target, reps=3, hit_masks=hit_masks,
                                       log=(lambda m: print(m, file=sys.stderr)) if rank == 0 else None)
     t_tune = time.perf_counter() - t_tune
     tw, th, bs, persist = best
     opts = _lib.default_opts(tile_w=tw, tile_h=th, batch_s=bs)
-    bstep = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, target, opts=opts, persistent=persist)
+    bstep = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, target, opts=opts, persistent=persist,
+                                hit_masks=hit_masks)
     rast = bstep.rast
     grad = bstep.grad
 
@@ -450,7 +456,8 @@ def main():
         h_grad = torch.empty(planes.shape, dtype=torch.float32).pin_memory()
         h_loss = torch.empty(V, dtype=torch.float32).pin_memory()
         twin = batched.BatchedStep(torch.empty_like(planes).copy_(planes), sc.n, sc.n_lobes, cams,
-                                   torch.empty_like(target).copy_(target), opts=opts, persistent=persist)
+                                   torch.empty_like(target).copy_(target), opts=opts, persistent=persist,
+                                   hit_masks=hit_masks)
         twin.capture()
         steps2 = [bstep, twin]
         cin, cout = torch.cuda.Stream(), torch.cuda.Stream()
@@ -613,7 +620,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{sc.n} Betas (256 planar sheets, 3 SB lobes), {V} views {scenes.describe_sizes(cams)} "
                                f"per GPU, fwd+bwd with per-view L1 loss, one CUDA-graph replay per step",
-                   "tile": f"{tw}x{th}", "batch_s": bs, "persistent": persist,
+                   "tile": f"{tw}x{th}", "batch_s": bs, "persistent": persist, "hit_masks": hit_masks,
                    "autotune": {"s": round(t_tune, 1), "ms": {f"{c[0]}x{c[1]}/S{c[2]}/{'P' if c[3] else 'G'}": round(v, 3)
                                                               for c, v in tune_ms.items()}},
                    "n_betas": sc.n, "views_per_gpu": V, "resolution": scenes.describe_sizes(cams),

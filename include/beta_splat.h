@@ -211,17 +211,33 @@ int beta_schedule(const beta_camera* cams, int32_t n_views, const beta_opts* opt
                   const uint32_t* tile_ranges, void* sched, const int32_t* d_status,
                   beta_stream_t stream);
 
+/* Bytes of the optional hit-mask buffer of beta_raster_fwd(_l1) and
+ * beta_raster_bwd for a pair capacity: per tile and per 32 list positions,
+ * one 32-bit word per pixel of the tile (which of the 32 primitives may cover
+ * that pixel) and one per 8x4 pixel block (which cover more than 12 of its
+ * pixels): ((pair_capacity >> 5) + total_tiles + 1) x (tile pixels x 33/32)
+ * x 4 bytes.  0 for invalid arguments. */
+size_t beta_hit_mask_bytes(const beta_camera* cams /* host */, int32_t n_views, const beta_opts* opt,
+                           int64_t pair_capacity);
+
 /* Step 3 (Eq. C): front-to-back compositing of every tile's sorted list.
  *   color     [3 x total_pixels] out: C + T_final * bg (planar per view)
  *   T_final   [total_pixels] out: final transmittance
  *   n_contrib [total_pixels] out: 1 + position (inside the tile's list) of
  *             the last primitive that contributed, 0 if none.
  *   sched     beta_schedule() output for a persistent launch, or NULL
+ *   hit_masks, hit_mask_bytes: NULL / 0, or a 4-byte aligned buffer of
+ *             beta_hit_mask_bytes() for the pair capacity of the binning;
+ *             the forward writes which primitives may cover each pixel, and
+ *             a beta_raster_bwd given the same buffer reads them instead of
+ *             working them out again (the results are the same either way;
+ *             parts of the lists beyond a shorter buffer are recomputed).
  *   d_status  in: if non-zero the kernel writes nothing. */
 int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                    const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
-                    uint32_t* n_contrib, const int32_t* d_status, beta_stream_t stream);
+                    const uint32_t* tile_ranges, void* sched, void* hit_masks, size_t hit_mask_bytes,
+                    float* color, float* T_final, uint32_t* n_contrib, const int32_t* d_status,
+                    beta_stream_t stream);
 
 /* beta_raster_fwd followed by beta_l1_loss in one pass: the forward kernel
  * computes the L1 term and dL_dcolor of each pixel it writes, and one partial
@@ -238,9 +254,10 @@ size_t beta_raster_fwd_l1_workspace_bytes(const beta_camera* cams /* host */, in
                                           const beta_opts* opt);
 int beta_raster_fwd_l1(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                        const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                       const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
-                       uint32_t* n_contrib, const float* target, float* loss, float* dL_dcolor,
-                       void* ws, size_t ws_bytes, const int32_t* d_status, beta_stream_t stream);
+                       const uint32_t* tile_ranges, void* sched, void* hit_masks, size_t hit_mask_bytes,
+                       float* color, float* T_final, uint32_t* n_contrib, const float* target, float* loss,
+                       float* dL_dcolor, void* ws, size_t ws_bytes, const int32_t* d_status,
+                       beta_stream_t stream);
 
 /* Per-pixel L1 loss of a batch of views (Sec. 3.4, the L1 term):
  *   loss[v] = mean over 3 W_v H_v of |color - target|   (device float[n_views], out)
@@ -252,12 +269,14 @@ int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color,
 
 /* Step 4a (backward of Eq. C): walks each pixel's list from its last
  * contributor down, recovering T by division, and accumulates ten per-record
- * sums with warp-reduced atomics into grad2d: in whitened coordinates
+ * sums with vector or warp-reduced atomics into grad2d: in whitened coordinates
  * (u, v) = L^-1 (x - mu') (Sigma' = L L^T) and with k = (dL/dalpha) alpha /
  * (1 - r^2) -- sum k (u, v, u^2, u v, v^2), sum (dL/dalpha) alpha, the same
  * times log2(1 - r^2), and sum alpha T dL/dC (3).  beta_project_bwd turns
  * them into d mu', d Sigma', d o, d beta and d colour.
  *   sched     beta_schedule() output (persistent launch) or NULL
+ *   hit_masks, hit_mask_bytes: the buffer the forward of these lists wrote
+ *             (beta_raster_fwd), or NULL / 0
  *   dL_dcolor [3 x total_pixels] in (layout of color)
  *   grad2d    [beta_grad2d_bytes()] in/out: one 48-byte slot per record (16-byte
  *             aligned buffer), ACCUMULATED.
@@ -265,8 +284,8 @@ int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color,
  *             beta_project_bwd clears every slot it consumes. */
 int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                    const uint32_t* tile_ranges, void* sched, const float* T_final,
-                    const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
+                    const uint32_t* tile_ranges, void* sched, const void* hit_masks, size_t hit_mask_bytes,
+                    const float* T_final, const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
                     const int32_t* d_status, beta_stream_t stream);
 
 /* Step 4b (backward of Sec. 3.2 / Sec. 3.3): chains the 2D gradients of every

@@ -49,6 +49,7 @@ EXPORTS = [
     "beta_schedule", "beta_adam_default_opts", "beta_adam_step", "beta_relocate_workspace_bytes",
     "beta_relocate", "beta_dssim_workspace_bytes", "beta_l1_dssim_loss",
     "beta_raster_fwd_l1_workspace_bytes", "beta_raster_fwd_l1", "beta_debug_scan_faults",
+    "beta_hit_mask_bytes",
 ]
 
 
@@ -115,12 +116,13 @@ def load(path: str = LIB_PATH):
             "beta_l1_workspace_bytes": (sz, [C, i32]),
             "beta_project": (ctypes.c_int, [P, C, i32, O, vp, vp]),
             "beta_bin_sort": (ctypes.c_int, [P, C, i32, O, vp, vp, i64, vp, vp, vp, vp, sz, vp]),
-            "beta_raster_fwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "beta_hit_mask_bytes": (sz, [C, i32, O, i64]),
+            "beta_raster_fwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, sz, vp, vp, vp, vp, vp]),
             "beta_l1_loss": (ctypes.c_int, [C, i32, vp, vp, vp, vp, vp, sz, vp]),
             "beta_raster_fwd_l1_workspace_bytes": (sz, [C, i32, O]),
-            "beta_raster_fwd_l1": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
-                                                  vp, sz, vp, vp]),
-            "beta_raster_bwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+            "beta_raster_fwd_l1": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, sz, vp, vp, vp, vp, vp,
+                                                  vp, vp, sz, vp, vp]),
+            "beta_raster_bwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, sz, vp, vp, vp, vp, vp, vp]),
             "beta_schedule_bytes": (sz, [C, i32, O]),
             "beta_schedule": (ctypes.c_int, [C, i32, O, vp, vp, vp, vp]),
             "beta_project_bwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp]),

@@ -32,7 +32,7 @@ def cache_path() -> str:
 
 def workload_key(n: int, n_lobes: int, cameras, device) -> str:
     res = ",".join(f"{c.width}x{c.height}" for c in cameras)
-    return f"v3;n={n};M={n_lobes};views={res};dev={torch.cuda.get_device_name(device)}"
+    return f"v4;n={n};M={n_lobes};views={res};dev={torch.cuda.get_device_name(device)}"
 
 
 def _load():
@@ -52,10 +52,10 @@ def _save(d):
     os.replace(tmp, p)
 
 
-def time_candidate(planes, n, n_lobes, cameras, target, cand, reps=5):
+def time_candidate(planes, n, n_lobes, cameras, target, cand, reps=5, hit_masks=True):
     tw, th, s, persist = cand
     opts = _lib.default_opts(tile_w=tw, tile_h=th, batch_s=s)
-    step = BatchedStep(planes, n, n_lobes, cameras, target, opts=opts, persistent=persist)
+    step = BatchedStep(planes, n, n_lobes, cameras, target, opts=opts, persistent=persist, hit_masks=hit_masks)
     step.step()
     step.check()
     stream = torch.cuda.current_stream()
@@ -71,10 +71,11 @@ def time_candidate(planes, n, n_lobes, cameras, target, cand, reps=5):
     return ms
 
 
-def tune(planes, n, n_lobes, cameras, target, candidates=None, reps=5, use_cache=True, log=None):
+def tune(planes, n, n_lobes, cameras, target, candidates=None, reps=5, use_cache=True, log=None,
+         hit_masks=True):
     """Returns (best candidate, {candidate: ms}).  Candidates are tuples
     (tile_w, tile_h, batch_s, persistent)."""
-    key = workload_key(n, n_lobes, cameras, planes.device)
+    key = workload_key(n, n_lobes, cameras, planes.device) + f";hm={int(hit_masks)}"
     cache = _load() if use_cache else {}
     if use_cache and key in cache:
         e = cache[key]
@@ -82,7 +83,7 @@ def tune(planes, n, n_lobes, cameras, target, candidates=None, reps=5, use_cache
     times = {}
     for cand in (candidates or CANDIDATES):
         t0 = time.perf_counter()
-        times[tuple(cand)] = time_candidate(planes, n, n_lobes, cameras, target, cand, reps)
+        times[tuple(cand)] = time_candidate(planes, n, n_lobes, cameras, target, cand, reps, hit_masks)
         if log:
             log(f"autotune {cand}: {times[tuple(cand)]:.3f} ms ({time.perf_counter() - t0:.1f} s)")
     best = min(times, key=times.get)

@@ -19,11 +19,12 @@ from .render import Rasterizer
 
 class BatchedStep:
     def __init__(self, planes: torch.Tensor, n: int, n_lobes: int, cameras, target: torch.Tensor,
-                 opts: _lib.BetaOpts | None = None, persistent: bool = True, headroom: float = 1.15):
+                 opts: _lib.BetaOpts | None = None, persistent: bool = True, headroom: float = 1.15,
+                 hit_masks: bool = True):
         self.planes = planes
         self.target = target
         self.rast = Rasterizer(n, planes.shape[1], n_lobes, cameras, opts, device=planes.device,
-                               persistent=persistent)
+                               persistent=persistent, hit_masks=hit_masks)
         self.grad = torch.zeros_like(planes)
         self.headroom = headroom
         self.graph = None

@@ -261,10 +261,18 @@ int beta_bin_sort_static(const beta_params* prm, const beta_camera* cams, int32_
                                      d_pair_count, d_status, ws, (cudaStream_t)stream));
 }
 
+size_t beta_hit_mask_bytes(const beta_camera* cams, int32_t n_views, const beta_opts* opt,
+                           int64_t pair_capacity) {
+  ViewTable vt;
+  if (pair_capacity < 0 || check_opts(opt) != BETA_OK || build_views(cams, n_views, opt, vt) != BETA_OK) return 0;
+  return hit_mask_bytes(vt, render_opts(opt), pair_capacity);
+}
+
 int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                    const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
-                    uint32_t* n_contrib, const int32_t* d_status, beta_stream_t stream) {
+                    const uint32_t* tile_ranges, void* sched, void* hit_masks, size_t hit_mask_bytes,
+                    float* color, float* T_final, uint32_t* n_contrib, const int32_t* d_status,
+                    beta_stream_t stream) {
   if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !color || !T_final ||
       !n_contrib || !d_status)
     return BETA_ERR_ARG;
@@ -274,8 +282,10 @@ int beta_raster_fwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
   if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
   ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
   if (sched && ((uintptr_t)sched & 3u)) return BETA_ERR_ARG;
+  if (hit_masks && ((uintptr_t)hit_masks & 3u)) return BETA_ERR_ARG;
+  const HitMasks hm{hit_masks ? (uint32_t*)hit_masks : nullptr, hit_masks ? hit_mask_bytes / 4 : 0};
   return cuda_status(launch_raster_fwd(vt, render_opts(opt), pb.rec, pair_vals, tile_ranges, color,
-                                       T_final, n_contrib, d_status, (uint32_t*)sched,
+                                       T_final, n_contrib, d_status, (uint32_t*)sched, hm,
                                        (cudaStream_t)stream));
 }
 
@@ -287,9 +297,10 @@ size_t beta_raster_fwd_l1_workspace_bytes(const beta_camera* cams, int32_t n_vie
 
 int beta_raster_fwd_l1(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                        const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                       const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
-                       uint32_t* n_contrib, const float* target, float* loss, float* dL_dcolor,
-                       void* ws, size_t ws_bytes, const int32_t* d_status, beta_stream_t stream) {
+                       const uint32_t* tile_ranges, void* sched, void* hit_masks, size_t hit_mask_bytes,
+                       float* color, float* T_final, uint32_t* n_contrib, const float* target, float* loss,
+                       float* dL_dcolor, void* ws, size_t ws_bytes, const int32_t* d_status,
+                       beta_stream_t stream) {
   if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !color || !T_final ||
       !n_contrib || !d_status || !target || !loss || !dL_dcolor)
     return BETA_ERR_ARG;
@@ -299,10 +310,12 @@ int beta_raster_fwd_l1(const beta_params* prm, const beta_camera* cams, int32_t 
   if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
   if (sched && ((uintptr_t)sched & 3u)) return BETA_ERR_ARG;
   if (!ws || ws_bytes < fwd_l1_ws_bytes(vt) || ((uintptr_t)ws & 3u)) return BETA_ERR_WORKSPACE;
+  if (hit_masks && ((uintptr_t)hit_masks & 3u)) return BETA_ERR_ARG;
   ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
+  const HitMasks hm{hit_masks ? (uint32_t*)hit_masks : nullptr, hit_masks ? hit_mask_bytes / 4 : 0};
   return cuda_status(launch_raster_fwd_l1(vt, render_opts(opt), pb.rec, pair_vals, tile_ranges, color,
                                           T_final, n_contrib, d_status, (uint32_t*)sched, target, loss,
-                                          dL_dcolor, (float*)ws, (cudaStream_t)stream));
+                                          dL_dcolor, (float*)ws, hm, (cudaStream_t)stream));
 }
 
 size_t beta_schedule_bytes(const beta_camera* cams, int32_t n_views, const beta_opts* opt) {
@@ -336,8 +349,8 @@ int beta_l1_loss(const beta_camera* cams, int32_t n_views, const float* color, c
 
 int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                     const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
-                    const uint32_t* tile_ranges, void* sched, const float* T_final,
-                    const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
+                    const uint32_t* tile_ranges, void* sched, const void* hit_masks, size_t hit_mask_bytes,
+                    const float* T_final, const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
                     const int32_t* d_status, beta_stream_t stream) {
   if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !T_final || !n_contrib ||
       !dL_dcolor || !grad2d || !d_status || !aligned16(grad2d))
@@ -348,9 +361,11 @@ int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
   if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
   ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
   if (sched && ((uintptr_t)sched & 3u)) return BETA_ERR_ARG;
+  if (hit_masks && ((uintptr_t)hit_masks & 3u)) return BETA_ERR_ARG;
+  const HitMasks hm{hit_masks ? (uint32_t*)hit_masks : nullptr, hit_masks ? hit_mask_bytes / 4 : 0};
   return cuda_status(launch_raster_bwd(vt, render_opts(opt), pb.rec, pair_vals, tile_ranges,
                                        T_final, n_contrib, dL_dcolor, grad2d, d_status,
-                                       (uint32_t*)sched, (cudaStream_t)stream));
+                                       (uint32_t*)sched, hm, (cudaStream_t)stream));
 }
 
 int beta_project_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,

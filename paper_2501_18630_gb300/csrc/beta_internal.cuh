@@ -383,14 +383,20 @@ size_t reloc_ws_bytes(int n);
 cudaError_t launch_relocate(int n, int pitch, int n_planes, float* planes, float* m, float* v,
                             const uint32_t* rnd, float min_opacity, void* ws, int32_t* src_out,
                             int32_t* d_count, cudaStream_t s);
+// optional hit-mask buffer shared by the raster forward and backward
+struct HitMasks {
+  uint32_t* words;   // nullptr: none (the backward recomputes its cover pass)
+  size_t n_words;
+};
+size_t hit_mask_bytes(const ViewTable& vt, const RenderOpts& ro, int64_t cap);
 cudaError_t launch_raster_fwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                               const uint32_t* vals, const uint32_t* ranges, float* color,
                               float* T_final, uint32_t* n_contrib, const int32_t* status,
-                              uint32_t* sched, cudaStream_t s);
+                              uint32_t* sched, HitMasks hm, cudaStream_t s);
 cudaError_t launch_raster_bwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                               const uint32_t* vals, const uint32_t* ranges, const float* T_final,
                               const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
-                              const int32_t* status, uint32_t* sched, cudaStream_t s);
+                              const int32_t* status, uint32_t* sched, HitMasks hm, cudaStream_t s);
 size_t schedule_bytes(int total_tiles);
 cudaError_t launch_schedule(const ViewTable& vt, const uint32_t* ranges, uint32_t* sched,
                             const int32_t* status, cudaStream_t s);
@@ -399,7 +405,7 @@ cudaError_t launch_raster_fwd_l1(const ViewTable& vt, const RenderOpts& ro, cons
                                  const uint32_t* vals, const uint32_t* ranges, float* color,
                                  float* T_final, uint32_t* n_contrib, const int32_t* status,
                                  uint32_t* sched, const float* target, float* loss, float* dL_dcolor,
-                                 float* ws, cudaStream_t s);
+                                 float* ws, HitMasks hm, cudaStream_t s);
 size_t l1_ws_bytes(const ViewTable& vt);
 cudaError_t launch_l1(const ViewTable& vt, const float* color, const float* target, float* loss,
                       float* dL_dcolor, float* ws, cudaStream_t s);

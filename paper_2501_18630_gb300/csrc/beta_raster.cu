@@ -63,6 +63,14 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
+// floor / ceil of x in [-1, 8] by one add rounded toward -inf / +inf: the
+// floats near 1.5 * 2^23 are spaced by 1, so the rounded sum is that constant
+// plus floor(x) / ceil(x) exactly (an FMA-pipe add instead of a round and a
+// conversion on the narrow multi-function pipe).
+constexpr float kRoundMagic = 12582912.0f;   // 1.5 * 2^23, bits 0x4B400000
+__device__ __forceinline__ int floor_small(float x) { return __float_as_int(__fadd_rd(x, kRoundMagic)) - 0x4B400000; }
+__device__ __forceinline__ int ceil_small(float x) { return __float_as_int(__fadd_ru(x, kRoundMagic)) - 0x4B400000; }
+
 // Pixels of the 8x4 block with first pixel (bxf, byf) whose centre the
 // record's support r^2 < 1 may cover: bit 8 r + j for row r, column j.  On a
 // row, r^2 = (p dx)^2 + (q2 dx + q1 dy)^2 is a convex quadratic in dx, so its
@@ -89,8 +97,8 @@ __device__ __forceinline__ uint32_t block_cover(float4 f0, float4 f1, float bxf,
     const float w = sqrt_approx(fmaxf(disc, 0.0f)) * iA;
     const float xc = fmaf(-sxc, dy, -X0);              // interval centre, in columns of the block
     const float e = fmaf(1e-5f, fabsf(xc) + w, 1e-3f);
-    const int ilo = (int)fminf(fmaxf(ceilf(xc - w - e), 0.0f), 8.0f);
-    const int ihi = (int)fmaxf(fminf(floorf(xc + w + e), 7.0f), -1.0f);
+    const int ilo = ceil_small(fminf(fmaxf(xc - w - e, 0.0f), 8.0f));     // in [0, 8]
+    const int ihi = floor_small(fmaxf(fminf(xc + w + e, 7.0f), -1.0f));   // in [-1, 7]
     const uint32_t row = (0xFFu >> (7 - ihi)) & (0xFFu << ilo);   // columns ilo .. ihi
     m |= (disc > 0.0f ? row : 0u) << (8 * r);
   }
@@ -147,6 +155,30 @@ __device__ __forceinline__ void stage_record(float4* dst, const float4* __restri
   for (int q = 0; q < kRecordF4; ++q) cp_async16(dst + q, src + q);
 }
 
+// Records covering more than this many pixels of a warp's block are reduced
+// across the warp before their atomics in the backward; for the others every
+// lane adds its own terms.
+constexpr int kLaneAtomics = 12;
+
+// Hit masks (optional, written by the forward, read by the backward): per
+// tile g, per chunk j of 32 list positions, NT words (word t: the records of
+// the chunk that may cover pixel t of the tile, bit k = position 32 j + k,
+// from block_cover and the transpose) and NW words (word w: the chunk's
+// records covering more than kLaneAtomics pixels of warp w's block).  Chunk j
+// of tile g is slot (ranges[g] >> 5) + g + j, so the slots of the tiles never
+// overlap and (pairs >> 5) + tiles + 1 slots hold every list.  A tile whose
+// slots do not all fit in the buffer uses none (the backward recomputes its
+// cover pass); returns the tile's first slot, or nullptr.
+template <int NT>
+__device__ __forceinline__ uint32_t* hit_tile(uint32_t* hm, size_t hm_words, uint32_t range0, uint32_t range1,
+                                              int g) {
+  constexpr int NW = NT / 32;
+  if (!hm) return nullptr;
+  const size_t w0 = ((size_t)(range0 >> 5) + (size_t)g) * (size_t)(NT + NW);
+  const size_t n = (size_t)((range1 - range0 + 31u) >> 5) * (size_t)(NT + NW);
+  return w0 + n <= hm_words ? hm + w0 : nullptr;
+}
+
 // Tile assignment: CTA b renders tile b, or (persistent) tiles are taken from
 // the schedule's counter in its longest-first order.  Returns -1 when done.
 template <bool PERSIST>
@@ -184,7 +216,8 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
                                                        uint32_t* ctr, const uint32_t* __restrict__ order,
                                                        const float* __restrict__ target,
                                                        float* __restrict__ dLdC,
-                                                       float* __restrict__ l1_partial) {
+                                                       float* __restrict__ l1_partial,
+                                                       uint32_t* __restrict__ hm, size_t hm_words) {
   constexpr int NT = TW * TH, BXW = TW / 8, RPT = (S + NT - 1) / NT;
   __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
   __shared__ float s_l1[NT / 32];
@@ -205,6 +238,7 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
     const bool inside = x < W && y < H;
     const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
     const uint32_t start = ranges[g], end = ranges[g + 1];
+    uint32_t* const hslot = hit_tile<NT>(hm, hm_words, start, end, g);
     if (target && inside) {
       const int64_t HW = (int64_t)W * H;
       const int64_t o = 3 * vt.v[v].pix_off + (int64_t)y * W + x;
@@ -252,6 +286,13 @@ __global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTa
         const int idx = c + lane;
         const uint32_t cov = idx < cnt ? block_cover(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
         uint32_t mine = transpose32(cov, lane);
+        if (hslot) {
+          // kept for the backward, which would otherwise redo this pass
+          uint32_t* slot = hslot + (size_t)((base - start + c) >> 5) * (NT + NT / 32);
+          const uint32_t wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
+          slot[tid] = mine;
+          if (lane == 0) slot[NT + warp] = wide;
+        }
         if (done) mine = 0u;   // off-image lanes start done and stay done
         // pass 2: every lane composites its own hits in list order, so the
         // warp iterates as often as its busiest lane, not once per record
@@ -370,11 +411,6 @@ __device__ __forceinline__ int warp_sum10_field(int lane) {
   return (b4 ? 5 : 0) + sub;
 }
 
-// Records covering more lanes than this are reduced across the warp before
-// their atomics; the others' lanes add their own terms (measured sweep of the
-// threshold: 8 / 12 / 16 / 20 lanes gave 4.01 / 3.80 / 3.83 / 4.03 ms).
-constexpr int kLaneAtomics = 12;
-
 // Per-lane terms of a record's 2D gradients at this lane's pixel, in whitened
 // coordinates (u, v) = L^-1 (x - mu'); beta, 1/o, ln 2 and the whitening
 // matrix are per-record constants applied by the projection backward:
@@ -426,7 +462,8 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
                                                        const float* __restrict__ dLdC,
                                                        float* __restrict__ grad2d,
                                                        const int32_t* __restrict__ status,
-                                                       uint32_t* ctr, const uint32_t* __restrict__ order) {
+                                                       uint32_t* ctr, const uint32_t* __restrict__ order,
+                                                       const uint32_t* __restrict__ hm, size_t hm_words) {
   constexpr int NT = TW * TH, NW = NT / 32, BXW = TW / 8, RPT = (S + NT - 1) / NT;
   __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
   __shared__ uint32_t s_ridx[2][S];
@@ -447,7 +484,9 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
     const int x = bx + (lane & 7), y = by + (lane >> 3);
     const bool inside = x < W && y < H;
     const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
-    const uint32_t* lst = vals + ranges[g];
+    const uint32_t range0 = ranges[g];
+    const uint32_t* lst = vals + range0;
+    const uint32_t* const hslot = hit_tile<NT>(const_cast<uint32_t*>(hm), hm_words, range0, ranges[g + 1], g);
 
     float T = 1.0f, gx = 0.0f, gy = 0.0f, gz = 0.0f, GS = 0.0f;
     uint32_t nl = 0;
@@ -469,43 +508,43 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
 #pragma unroll
     for (int w = 0; w < NW; ++w) bmax = max(bmax, (int)s_wmax[w]);
 
-    // Batches cover list positions [max(0, top - S), top) for top = bmax,
-    // bmax - S, ...  The first goes to buffer 0 now; the list entries of the
-    // second are loaded ahead so that its copies issue without waiting.
+    // Batch b covers list positions [b S, min(b S + S, bmax)), b = nb - 1 .. 0
+    // (the forward's batches, so chunks start at multiples of 32).  The last
+    // goes to buffer 0 now; the list entries of the one before it are loaded
+    // ahead so that its copies issue without waiting.
+    const int nb = (bmax + S - 1) / S;
     uint32_t rn[RPT];
     {
-      const int lo0 = max(0, bmax - S), lo1 = max(0, bmax - 2 * S);
+      const int lo0 = (nb - 1) * S, lo1 = lo0 - S;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int jj = tid + q * NT;
-        if (jj < bmax - lo0) {
+        if (nb > 0 && jj < bmax - lo0) {
           const uint32_t r = lst[lo0 + jj];
           s_ridx[0][jj] = r;
           stage_record(s_rec[0][jj], rec, r);
         }
-        rn[q] = (jj < bmax - S - lo1) ? lst[lo1 + jj] : 0u;
+        rn[q] = (lo1 >= 0 && jj < S) ? lst[lo1 + jj] : 0u;
       }
       cp_async_commit();
     }
 
     int buf = 0;
-    for (int top = bmax; top > 0; top -= S) {
-      const int lo = max(0, top - S);
-      const int cnt = top - lo;
+    for (int b = nb - 1; b >= 0; --b) {
+      const int lo = b * S;
+      const int cnt = min(S, bmax - lo);
       cp_async_wait_all();
       __syncthreads();
       {
-        // copies of the next batch into the other buffer, entries of the one after
-        const int t1 = top - S, lo1 = max(0, t1 - S);
-        const int t2 = top - 2 * S, lo2 = max(0, t2 - S);
+        // copies of batch b - 1 (full) into the other buffer, entries of b - 2
 #pragma unroll
         for (int q = 0; q < RPT; ++q) {
           const int jj = tid + q * NT;
-          if (jj < t1 - lo1) {
+          if (b >= 1 && jj < S) {
             s_ridx[buf ^ 1][jj] = rn[q];
             stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
           }
-          rn[q] = (jj < t2 - lo2) ? lst[lo2 + jj] : 0u;
+          rn[q] = (b >= 2 && jj < S) ? lst[(b - 2) * S + jj] : 0u;
         }
         cp_async_commit();
       }
@@ -515,11 +554,19 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
         // c + k may cover (records at or past the warp's last contributor
         // are skipped); records covering more than kLaneAtomics pixels are
         // marked `wide`; the transpose gives every lane its own records
-        const int idx = c + lane;
-        const uint32_t cov = (idx < cnt && (uint32_t)(lo + idx) < wmax)
-                                 ? block_cover(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
-        uint32_t wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
-        uint32_t mine = transpose32(cov, lane);
+        uint32_t wide, mine;
+        if (hslot) {
+          const uint32_t* slot = hslot + (size_t)((lo + c) >> 5) * (NT + NW);
+          mine = slot[tid];                              // the forward's pass 1
+          const int limw = (int)wmax - (lo + c);         // no lane of the warp reaches past wmax
+          wide = slot[NT + warp] & (limw >= 32 ? 0xffffffffu : (1u << limw) - 1u);
+        } else {
+          const int idx = c + lane;
+          const uint32_t cov = (idx < cnt && (uint32_t)(lo + idx) < wmax)
+                                   ? block_cover(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
+          wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
+          mine = transpose32(cov, lane);
+        }
         const int lim = (int)nl - (lo + c);            // only positions before this pixel's last contributor
         mine &= lim >= 32 ? 0xffffffffu : (lim <= 0 ? 0u : (1u << lim) - 1u);
         // pass 2, in reverse list order: between wide records every lane walks
@@ -701,16 +748,16 @@ template <int TW, int TH, int S>
 cudaError_t fwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                       const uint32_t* vals, const uint32_t* ranges, float* color, float* T_final,
                       uint32_t* n_contrib, const int32_t* status, uint32_t* sched, const float* target,
-                      float* dL_dcolor, float* l1_partial, cudaStream_t s) {
+                      float* dL_dcolor, float* l1_partial, HitMasks hm, cudaStream_t s) {
   if (sched) {
     auto k = k_raster_fwd<TW, TH, S, true>;
     k<<<persistent_grid(k, TW * TH, vt.total_tiles), TW * TH, 0, s>>>(
         vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched + 0, sched + kSchedOrder,
-        target, dL_dcolor, l1_partial);
+        target, dL_dcolor, l1_partial, hm.words, hm.n_words);
   } else {
     k_raster_fwd<TW, TH, S, false><<<vt.total_tiles, TW * TH, 0, s>>>(
         vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, nullptr, nullptr, target, dL_dcolor,
-        l1_partial);
+        l1_partial, hm.words, hm.n_words);
   }
   return cudaGetLastError();
 }
@@ -719,15 +766,16 @@ template <int TW, int TH, int S>
 cudaError_t bwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                       const uint32_t* vals, const uint32_t* ranges, const float* T_final,
                       const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
-                      const int32_t* status, uint32_t* sched, cudaStream_t s) {
+                      const int32_t* status, uint32_t* sched, HitMasks hm, cudaStream_t s) {
   if (sched) {
     auto k = k_raster_bwd<TW, TH, S, true>;
     k<<<persistent_grid(k, TW * TH, vt.total_tiles), TW * TH, 0, s>>>(
         vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, sched + 2,
-        sched + kSchedOrder);
+        sched + kSchedOrder, hm.words, hm.n_words);
   } else {
     k_raster_bwd<TW, TH, S, false><<<vt.total_tiles, TW * TH, 0, s>>>(
-        vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, nullptr, nullptr);
+        vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, nullptr, nullptr,
+        hm.words, hm.n_words);
   }
   return cudaGetLastError();
 }
@@ -761,10 +809,16 @@ cudaError_t bwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* r
 cudaError_t launch_raster_fwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                               const uint32_t* vals, const uint32_t* ranges, float* color,
                               float* T_final, uint32_t* n_contrib, const int32_t* status,
-                              uint32_t* sched, cudaStream_t s) {
+                              uint32_t* sched, HitMasks hm, cudaStream_t s) {
   if (vt.total_tiles <= 0) return cudaSuccess;
   BETA_TILE_DISPATCH(fwd_shape, vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched,
-                     nullptr, nullptr, nullptr, s)
+                     nullptr, nullptr, nullptr, hm, s)
+}
+
+size_t hit_mask_bytes(const ViewTable& vt, const RenderOpts& ro, int64_t cap) {
+  const int64_t nt = (int64_t)ro.tile_w * ro.tile_h;
+  const int64_t slots = (std::max<int64_t>(cap, 0) >> 5) + vt.total_tiles + 1;
+  return (size_t)slots * (size_t)(nt + nt / 32) * sizeof(uint32_t);
 }
 
 size_t fwd_l1_ws_bytes(const ViewTable& vt) { return (size_t)std::max(vt.total_tiles, 1) * sizeof(float); }
@@ -775,12 +829,12 @@ cudaError_t launch_raster_fwd_l1(const ViewTable& vt_in, const RenderOpts& ro, c
                                  const uint32_t* vals, const uint32_t* ranges, float* color,
                                  float* T_final, uint32_t* n_contrib, const int32_t* status,
                                  uint32_t* sched, const float* target, float* loss, float* dL_dcolor,
-                                 float* ws, cudaStream_t s) {
+                                 float* ws, HitMasks hm, cudaStream_t s) {
   if (vt_in.total_tiles <= 0) return cudaSuccess;
   cudaError_t e = [&]() -> cudaError_t {
     const ViewTable& vt = vt_in;
     BETA_TILE_DISPATCH(fwd_shape, vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched,
-                       target, dL_dcolor, ws, s)
+                       target, dL_dcolor, ws, hm, s)
   }();
   if (e != cudaSuccess) return e;
   ViewTable vt = vt_in;   // the reduce finds view v's partials from tile_off[v]
@@ -792,10 +846,10 @@ cudaError_t launch_raster_fwd_l1(const ViewTable& vt_in, const RenderOpts& ro, c
 cudaError_t launch_raster_bwd(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
                               const uint32_t* vals, const uint32_t* ranges, const float* T_final,
                               const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
-                              const int32_t* status, uint32_t* sched, cudaStream_t s) {
+                              const int32_t* status, uint32_t* sched, HitMasks hm, cudaStream_t s) {
   if (vt.total_tiles <= 0) return cudaSuccess;
   BETA_TILE_DISPATCH(bwd_shape, vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d,
-                     status, sched, s)
+                     status, sched, hm, s)
 }
 
 // the L1 block offsets of each view ride in ViewDev::pad0

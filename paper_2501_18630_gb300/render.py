@@ -27,7 +27,8 @@ class Rasterizer:
     forward overwrites the saved per-pixel state of the first."""
 
     def __init__(self, n, pitch, n_lobes, cameras, opts: _lib.BetaOpts | None = None,
-                 pair_capacity: int | None = None, device="cuda", persistent: bool = False):
+                 pair_capacity: int | None = None, device="cuda", persistent: bool = False,
+                 hit_masks: bool = False):
         self.L = _lib.load()
         self.n, self.pitch, self.n_lobes = int(n), int(pitch), int(n_lobes)
         self.cameras = list(cameras)
@@ -60,6 +61,11 @@ class Rasterizer:
         self.l1_ws = torch.empty(max(4, int(L.beta_l1_workspace_bytes(self.cams, self.V))), dtype=torch.uint8, device=dev)
         nb = int(L.beta_raster_fwd_l1_workspace_bytes(self.cams, self.V, ctypes.byref(self.opts)))
         self.fwd_l1_ws = torch.empty(max(4, nb), dtype=torch.uint8, device=dev)
+        # hit masks: the forward keeps which Betas may cover each pixel for the
+        # backward (about 16 bytes per pixel on the sheet scenes); off, the
+        # backward works them out again
+        self.use_hit_masks = bool(hit_masks)
+        self.hit_masks = None
         cap = pair_capacity if pair_capacity is not None else max(1 << 16, 4 * self.n * self.V)
         self._alloc_pairs(cap)
         self.persistent = bool(persistent)
@@ -75,6 +81,15 @@ class Rasterizer:
         self.pair_vals = torch.empty(max(cap, 1), dtype=torch.int32, device=self.device)
         ws = int(self.L.beta_binsort_workspace_bytes(self.pitch, self.V, cap, self.cams, ctypes.byref(self.opts)))
         self.sort_ws = torch.empty(max(ws, 256), dtype=torch.uint8, device=self.device)
+        if self.use_hit_masks:
+            self.hit_masks = None
+            nb = int(self.L.beta_hit_mask_bytes(self.cams, self.V, ctypes.byref(self.opts), cap))
+            self.hit_masks = torch.empty(max(nb, 4) // 4, dtype=torch.int32, device=self.device)
+
+    def _hm(self):
+        if self.hit_masks is None:
+            return ctypes.c_void_p(0), 0
+        return _vp(self.hit_masks), self.hit_masks.numel() * 4
 
     def params(self, planes: torch.Tensor) -> _lib.BetaParams:
         assert planes.is_cuda and planes.dtype == torch.float32 and planes.is_contiguous()
@@ -113,18 +128,20 @@ class Rasterizer:
 
     def raster_fwd(self, planes):
         prm = self.params(planes)
+        hm, hb = self._hm()
         _lib.check("beta_raster_fwd", self.L.beta_raster_fwd(
             ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
-            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), _vp(self.color),
+            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), hm, hb, _vp(self.color),
             _vp(self.T_final), _vp(self.n_contrib), _vp(self.status), _stream()))
 
     def raster_fwd_l1(self, planes, target: torch.Tensor):
         """raster_fwd and l1_loss in one pass (the L1 term in the forward's epilogue)."""
         assert target.numel() == self.color.numel() and target.is_contiguous()
         prm = self.params(planes)
+        hm, hb = self._hm()
         _lib.check("beta_raster_fwd_l1", self.L.beta_raster_fwd_l1(
             ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
-            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), _vp(self.color),
+            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), hm, hb, _vp(self.color),
             _vp(self.T_final), _vp(self.n_contrib), _vp(target), _vp(self.loss), _vp(self.dL_dcolor),
             _vp(self.fwd_l1_ws), self.fwd_l1_ws.numel(), _vp(self.status), _stream()))
         return self.loss, self.dL_dcolor
@@ -150,9 +167,10 @@ class Rasterizer:
     def raster_bwd(self, planes, dL_dcolor):
         prm = self.params(planes)
         assert dL_dcolor.numel() == self.color.numel() and dL_dcolor.is_contiguous()
+        hm, hb = self._hm()
         _lib.check("beta_raster_bwd", self.L.beta_raster_bwd(
             ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
-            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), _vp(self.T_final),
+            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), hm, hb, _vp(self.T_final),
             _vp(self.n_contrib), _vp(dL_dcolor), _vp(self.grad2d), _vp(self.status), _stream()))
 
     def project_bwd(self, planes, grad_planes):

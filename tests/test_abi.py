@@ -70,6 +70,10 @@ def test_host_queries(L):
     assert L.beta_l1_workspace_bytes(arr, 2) >= 4 * ((1297 * 840 + 255) // 256)
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert L.beta_status_string(code)
+    # hit masks: per 32 pairs of capacity and per tile, one word per tile pixel and per 8x4 block
+    tiles = 82 * 53 + 16 * 16
+    assert L.beta_hit_mask_bytes(arr, 2, ctypes.byref(o), 10000) == ((10000 >> 5) + tiles + 1) * (256 + 8) * 4
+    assert L.beta_hit_mask_bytes(arr, 2, ctypes.byref(o), -1) == 0
 
 
 def test_argument_errors_are_returned_without_launch(L):

@@ -168,3 +168,36 @@ def test_view_split_gradients_sum_to_full_batch():
     scale = np.abs(g_all).max(axis=1, keepdims=True) + 1e-30
     assert np.all(np.abs(g_all).max(axis=1) > 0)
     assert np.max(np.abs(g_a + g_b - g_all) / scale) < 1e-4
+
+
+@pytest.mark.parametrize("tw,th,bs,persist", [(16, 8, 128, False), (16, 16, 256, True), (8, 8, 64, False),
+                                              (32, 16, 128, True)])
+def test_hit_masks_give_the_same_results(tw, th, bs, persist):
+    """With the hit-mask buffer the forward keeps, per pixel, which Betas may
+    cover it and the backward reads that instead of redoing its cover pass:
+    images, T and n_contrib bit for bit, gradients within 1e-4 of each
+    plane's largest value (atomics add in another order).  A buffer too short
+    for the whole list (the backward recomputes the rest) gives the same."""
+    sc = scenes.config_scene(3, n=60_000)
+    cams = [scenes.ring_camera(4.0, 15.0, 0.7, 333, 201), scenes.ring_camera(4.0, 15.0, 2.2, 160, 97)]
+    tgt = torch.from_numpy(np.concatenate([t.reshape(-1) for t in scenes.target_images(cams, seed=5)])).cuda()
+    gc.ensure_built()
+    planes = torch.from_numpy(sc.planes).cuda()
+    opts = _lib.default_opts(tile_w=tw, tile_h=th, batch_s=bs)
+    out = []
+    for mode in ("none", "full", "short"):
+        r = render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, cams, opts, persistent=persist,
+                              hit_masks=mode != "none")
+        r.forward(planes)
+        if mode == "short":
+            r.hit_masks = r.hit_masks[: r.hit_masks.numel() // 3]
+            r.raster_fwd(planes)
+        _, d = r.l1_loss(tgt)
+        g = r.backward(planes, d)
+        torch.cuda.synchronize()
+        out.append((r.color.clone(), r.T_final.clone(), r.n_contrib.clone(), g.cpu().numpy()[:, :sc.n]))
+    (c0, t0, n0, g0) = out[0]
+    scale = np.abs(g0).max(axis=1, keepdims=True) + 1e-30
+    for (c, t, n_, g) in out[1:]:
+        assert torch.equal(c, c0) and torch.equal(t, t0) and torch.equal(n_, n0)
+        assert np.max(np.abs(g - g0) / scale) < 1e-4

@@ -35,7 +35,7 @@ def test_6m_betas_eight_4k_views_in_budget():
     base = torch.cuda.memory_allocated()
     planes = torch.from_numpy(sc.planes).cuda()
     tgt = torch.from_numpy(np.concatenate([t.reshape(-1) for t in scenes.target_images(sc.cameras, seed=6)])).cuda()
-    step = batched.BatchedStep(planes, sc.n, sc.n_lobes, sc.cameras, tgt)
+    step = batched.BatchedStep(planes, sc.n, sc.n_lobes, sc.cameras, tgt, hit_masks=False)
     step.step()
     k = step.check()
     torch.cuda.synchronize()
