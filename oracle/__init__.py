@@ -87,7 +87,7 @@ def lib():
             L.oracle_rule_rects.restype = None
             L.oracle_rule_rects.argtypes = [fp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.POINTER(OCam), ctypes.c_float, ctypes.c_float,
-                                            ctypes.c_float, ctypes.c_int32, ctypes.c_int32, ip, up, ip]
+                                            ctypes.c_float, ctypes.c_int32, ctypes.c_int32, ip, up, ip, up]
             _lib = L
     return _lib
 
@@ -190,21 +190,45 @@ def rule_opacity(logit) -> np.ndarray:
     return out
 
 
-def rule_rects(planes, n, n_lobes, cam, blur_eps=0.0, tile_w=16, tile_h=16, b_lo=-np.inf, b_hi=np.inf):
-    """Rule B1 rectangles (n,4) = (tx0, tx1, ty0, ty1), rule D keys (n,), binned flags (n,).
-    Primitives with b outside [b_lo, b_hi) are not binned (geometry decomposition)."""
+def rule_rects(planes, n, n_lobes, cam, blur_eps=0.0, tile_w=16, tile_h=16, b_lo=-np.inf, b_hi=np.inf,
+               with_tiles=False):
+    """Rule B1 rectangles (n,4) = (tx0, tx1, ty0, ty1), rule D keys (n,), binned flags (n,),
+    and with with_tiles the rule B2 tile masks (n,) of the rectangles (bit r w + q for tile
+    (tx0 + q, ty0 + r); 0xFFFFFFFF: every tile).  Primitives with b outside [b_lo, b_hi)
+    are not binned (geometry decomposition)."""
     L = lib()
     p = np.ascontiguousarray(planes, dtype=np.float32)
     rects = np.zeros((max(n, 1), 4), np.int32)
     keys = np.zeros(max(n, 1), np.uint32)
     binned = np.zeros(max(n, 1), np.int32)
+    tiles = np.zeros(max(n, 1), np.uint32)
     oc = make_cam(cam)
     L.oracle_rule_rects(_ptr(p, ctypes.c_float), n, p.shape[1], n_lobes, ctypes.byref(oc),
                         ctypes.c_float(np.float32(blur_eps)), ctypes.c_float(np.float32(b_lo)),
                         ctypes.c_float(np.float32(b_hi)), tile_w, tile_h,
                         _ptr(rects, ctypes.c_int32), _ptr(keys, ctypes.c_uint32),
-                        _ptr(binned, ctypes.c_int32))
+                        _ptr(binned, ctypes.c_int32), _ptr(tiles, ctypes.c_uint32))
+    if with_tiles:
+        return rects[:n], keys[:n], binned[:n], tiles[:n]
     return rects[:n], keys[:n], binned[:n]
+
+
+def expand_tiles(rects, tiles):
+    """(primitive row, tx, ty) of every tile a primitive's rule B2 mask keeps
+    inside its rectangle, in rectangle row-major order."""
+    r = rects.astype(np.int64)
+    w = r[:, 1] - r[:, 0] + 1
+    h = r[:, 3] - r[:, 2] + 1
+    cnt = w * h
+    rw = np.repeat(np.arange(len(r)), cnt)
+    local = np.arange(cnt.sum(), dtype=np.int64) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+    full = np.repeat(cnt > 32, cnt)
+    bit = (tiles.astype(np.uint64)[rw] >> np.minimum(local, 31).astype(np.uint64)) & np.uint64(1)
+    keep = full | (bit == 1)
+    rw, local = rw[keep], local[keep]
+    ty = r[rw, 2] + local // w[rw]
+    tx = r[rw, 0] + local % w[rw]
+    return rw, tx, ty
 
 
 def n_tiles(cam, tile_w=16, tile_h=16):
@@ -213,7 +237,8 @@ def n_tiles(cam, tile_w=16, tile_h=16):
 
 def bin_pairs(planes, n, n_lobes, cams, blur_eps=0.0, tile_w=16, tile_h=16, pitch=None,
               b_lo=-np.inf, b_hi=np.inf):
-    """Sorted (global tile, record) pairs of a batch of views.
+    """Sorted (global tile, record) pairs of a batch of views: one pair per
+    tile of a primitive's rule B1 rectangle that its rule B2 mask keeps.
 
     A record is view * pitch + primitive.  Global tiles are numbered view by
     view, row-major inside a view.  The order is (tile, depth key, primitive
@@ -224,18 +249,12 @@ def bin_pairs(planes, n, n_lobes, cams, blur_eps=0.0, tile_w=16, tile_h=16, pitc
     all_tiles, all_keys, all_rec = [], [], []
     tile_off = 0
     for v, cam in enumerate(cams):
-        rects, keys, binned = rule_rects(planes, n, n_lobes, cam, blur_eps, tile_w, tile_h, b_lo, b_hi)
+        rects, keys, binned, masks = rule_rects(planes, n, n_lobes, cam, blur_eps, tile_w, tile_h, b_lo, b_hi,
+                                                with_tiles=True)
         ntx, nty = n_tiles(cam, tile_w, tile_h)
         idx = np.nonzero(binned)[0]
-        r = rects[idx].astype(np.int64)
-        wx = r[:, 1] - r[:, 0] + 1
-        cnt = wx * (r[:, 3] - r[:, 2] + 1)
-        prim = np.repeat(idx, cnt)
-        first = np.repeat(np.cumsum(cnt) - cnt, cnt)
-        local = np.arange(cnt.sum(), dtype=np.int64) - first
-        rw = np.repeat(np.arange(len(idx)), cnt)
-        ty = r[rw, 2] + local // wx[rw]
-        tx = r[rw, 0] + local % wx[rw]
+        rw, tx, ty = expand_tiles(rects[idx], masks[idx])
+        prim = idx[rw]
         all_tiles.append(tile_off + ty * ntx + tx)
         all_keys.append(keys[prim].astype(np.int64))
         all_rec.append(v * pitch + prim.astype(np.int64))

@@ -371,13 +371,116 @@ void oracle_rule_opacity(const float* logit, int32_t n, float* o) {
   }
 }
 
+/* a*b - c*d with Kahan's fused multiply-add algorithm (one rounding error) */
+static float rule_dop(float a, float b, float c, float d) {
+  float w = c * d;
+  float e = fmaf(-c, d, w);
+  float f = fmaf(a, b, -w);
+  return f + e;
+}
+
+/* Rule B2: which tiles of the rule B1 rectangle the support ellipse reaches
+ * (Sec. 3.1 / Eq. 2: the Beta kernel is exactly zero outside r^2 < 1, so a
+ * tile no pixel centre of which lies inside the support gets no pair).
+ * For every tile row, the band of its pixel-centre rows (widened by PAD) is
+ * cut with the ellipse of Sigma' inflated by INFL; the ellipse's x-range over
+ * the band is the whole half-width when its rightmost (leftmost) point lies in
+ * the band, else the boundary at the band end nearest that point; the columns
+ * whose centres lie within that range widened by PAD give the row's tiles.
+ * Sigma' = [[a, b], [b, c]] with a = sxx, c = syy (blur included),
+ * b = M0 . M1 and det = |M0 x M1|^2 + blur (a + c - blur), minors by Kahan's
+ * algorithm; at height y (from the centre) the boundary is
+ *   x = (b / c) y +- sqrt(K2 (det / c) max(0, 1 - y^2 / (K2 c))),  K2 = INFL^2.
+ * Every operation is fp32, rounded to nearest, in the order written.  Returns
+ * the tiles as bit r w + q for tile (tx0 + q, ty0 + r) of a w x h rectangle,
+ * or 0xFFFFFFFF (every tile) when w h > 32 or the ellipse is degenerate. */
+static uint32_t rule_tiles(const float M0[3], const float M1[3], float sxx, float syy, float blur,
+                           float pxc, float pyc, const int32_t rect[4], int32_t width, int32_t height,
+                           int32_t tile_w, int32_t tile_h) {
+  const int32_t w = rect[1] - rect[0] + 1, h = rect[3] - rect[2] + 1;
+  if (w * h > 32) return 0xFFFFFFFFu;
+  if (!(sxx > 0.0f && syy > 0.0f)) return 0xFFFFFFFFu;
+  const float INFL = 1.000244140625f; /* 1 + 2^-12 */
+  const float PAD = 0.015625f;        /* 2^-6 pixel */
+  float b = M0[0] * M1[0];
+  b = b + M0[1] * M1[1];
+  b = b + M0[2] * M1[2];
+  float m01 = rule_dop(M0[0], M1[1], M0[1], M1[0]);
+  float m02 = rule_dop(M0[0], M1[2], M0[2], M1[0]);
+  float m12 = rule_dop(M0[1], M1[2], M0[2], M1[1]);
+  float det = m01 * m01;
+  det = det + m02 * m02;
+  det = det + m12 * m12;
+  det = det + blur * ((sxx + syy) - blur);
+  float sa = sqrtf(sxx), sc = sqrtf(syy);
+  float xfull = sa * INFL;
+  float ytop = sc * INFL;
+  float ystar = (b * INFL) / sa;
+  float slope = b / syy;
+  float K2 = INFL * INFL;
+  float hh = (det / syy) * K2;
+  float cc = syy * K2;
+  if (!(isfinite(ystar) && isfinite(slope) && isfinite(hh) && isfinite(cc) && cc > 0.0f)) return 0xFFFFFFFFu;
+  uint32_t mask = 0u;
+  for (int32_t r = 0; r < h; ++r) {
+    int32_t y0 = (rect[2] + r) * tile_h;
+    int32_t y1 = y0 + tile_h - 1;
+    if (y1 > height - 1) y1 = height - 1;
+    float ya = (((float)y0 + 0.5f) - PAD) - pyc;
+    float yb = (((float)y1 + 0.5f) + PAD) - pyc;
+    if (ya < -ytop) ya = -ytop;
+    if (yb > ytop) yb = ytop;
+    if (!(ya <= yb)) continue;
+    int in_r = (ya <= ystar) && (ystar <= yb);
+    int in_l = (ya <= -ystar) && (-ystar <= yb);
+    float yr = ystar < ya ? ya : yb;     /* band end nearest the rightmost point */
+    float yl = -ystar < ya ? ya : yb;    /* band end nearest the leftmost point  */
+    float xmax, xmin;
+    if (in_r) {
+      xmax = xfull;
+    } else {
+      float t = 1.0f - (yr * yr) / cc;
+      if (t < 0.0f) t = 0.0f;
+      xmax = slope * yr + sqrtf(hh * t);
+    }
+    if (in_l) {
+      xmin = -xfull;
+    } else {
+      float t = 1.0f - (yl * yl) / cc;
+      if (t < 0.0f) t = 0.0f;
+      xmin = slope * yl - sqrtf(hh * t);
+    }
+    float lo = ((pxc + xmin) - PAD) - 0.5f;
+    float hi = ((pxc + xmax) + PAD) - 0.5f;
+    uint32_t rowbits;
+    if (!(isfinite(lo) && isfinite(hi))) {
+      rowbits = w == 32 ? 0xFFFFFFFFu : ((1u << w) - 1u);
+    } else {
+      float i0 = floorf(lo) + 1.0f, i1 = ceilf(hi) - 1.0f;
+      if (i0 < 0.0f) i0 = 0.0f;
+      if (i1 > (float)(width - 1)) i1 = (float)(width - 1);
+      if (i0 > i1) continue;
+      int32_t q0 = (int32_t)i0 / tile_w, q1 = (int32_t)i1 / tile_w;
+      if (q0 < rect[0]) q0 = rect[0];
+      if (q1 > rect[1]) q1 = rect[1];
+      if (q0 > q1) continue;
+      q0 -= rect[0];
+      q1 -= rect[0];
+      rowbits = ((2u << q1) - 1u) & ~((1u << q0) - 1u);
+    }
+    mask |= rowbits << (r * w);
+  }
+  return mask;
+}
+
 /* Tile rectangle of primitive i under rule B1.  rect = (tx0, tx1, ty0, ty1),
  * inclusive tile indices, tx0 > tx1 when the primitive touches no tile.
  * Returns 1 if the primitive is binned, 0 otherwise.  key receives the
- * rule D depth key. */
+ * rule D depth key, tiles (if not NULL) the rule B2 tiles of the rectangle. */
 int32_t oracle_rule_rect_one(const float* planes, int32_t pitch, int32_t n_lobes, int32_t i,
                              const ocam* cam, float blur, float b_lo, float b_hi, int32_t tile_w,
-                             int32_t tile_h, int32_t rect[4], uint32_t* key) {
+                             int32_t tile_h, int32_t rect[4], uint32_t* key, uint32_t* tiles) {
+  if (tiles) *tiles = 0u;
   rect[0] = 0;
   rect[1] = -1;
   rect[2] = 0;
@@ -493,13 +596,15 @@ int32_t oracle_rule_rect_one(const float* planes, int32_t pitch, int32_t n_lobes
   rect[1] = (int32_t)i1 / tile_w;
   rect[2] = (int32_t)j0 / tile_h;
   rect[3] = (int32_t)j1 / tile_h;
+  if (tiles)
+    *tiles = rule_tiles(M0, M1, sxx, syy, blur, pxc, pyc, rect, cam->width, cam->height, tile_w, tile_h);
   return 1;
 }
 
 void oracle_rule_rects(const float* planes, int32_t n, int32_t pitch, int32_t n_lobes,
                        const ocam* cam, float blur, float b_lo, float b_hi, int32_t tile_w,
-                       int32_t tile_h, int32_t* rects, uint32_t* keys, int32_t* binned) {
+                       int32_t tile_h, int32_t* rects, uint32_t* keys, int32_t* binned, uint32_t* tiles) {
   for (int32_t i = 0; i < n; ++i)
     binned[i] = oracle_rule_rect_one(planes, pitch, n_lobes, i, cam, blur, b_lo, b_hi, tile_w,
-                                     tile_h, rects + 4 * (size_t)i, keys + i);
+                                     tile_h, rects + 4 * (size_t)i, keys + i, tiles ? tiles + i : NULL);
 }

@@ -561,12 +561,126 @@ def test_rule_b1_rect_is_conservative_and_tight(cfg, n):
     assert checked > n // 4
 
 
+def _min_r2_on_rect(Q, mx, my, x0, x1, y0, y1):
+    """Minimum of the convex r^2 = d^T Q d (d = p - mu) over the rectangle
+    [x0, x1] x [y0, y1] (FP64, closed form: the interior minimum if the centre
+    is inside, else the least of the four edge minima)."""
+    A, B, C = Q
+    if x0 <= mx <= x1 and y0 <= my <= y1:
+        return 0.0
+    best = np.inf
+    for yy in (y0, y1):          # horizontal edges: minimise over x
+        dy = yy - my
+        dx = float(np.clip(-B * dy / A, x0 - mx, x1 - mx))
+        best = min(best, A * dx * dx + 2 * B * dx * dy + C * dy * dy)
+    for xx in (x0, x1):          # vertical edges: minimise over y
+        dx = xx - mx
+        dy = float(np.clip(-B * dx / C, y0 - my, y1 - my))
+        best = min(best, A * dx * dx + 2 * B * dx * dy + C * dy * dy)
+    return best
+
+
+def _check_b2(planes, n, n_lobes, cam, tw, th, blur=0.0, stride=1):
+    """Rule B2 against FP64: every pixel with r^2 < 1 lies in a kept tile
+    (conservative), and every kept tile's rectangle of pixel centres comes
+    within r^2 < 1.002 of the support once widened by 1/32 pixel (tight: only
+    the rule's inflation and padding separate it from the ellipse).  Returns
+    (primitives checked, tiles kept, tiles of the rectangles)."""
+    pr = oracle.project(planes, n, n_lobes, cam, blur_eps=blur)
+    rects, _, binned, masks = oracle.rule_rects(planes, n, n_lobes, cam, blur, tw, th, with_tiles=True)
+    checked = kept_total = rect_total = 0
+    for i in range(0, n, stride):
+        if not binned[i]:
+            continue
+        a, b, c = pr["cov"][i]
+        mx, my = pr["mu2"][i]
+        Q = pr["conic"][i]
+        r = rects[i]
+        w, h = r[1] - r[0] + 1, r[3] - r[2] + 1
+        full = w * h > 32
+        kept = set()
+        for k in range(w * h):
+            if full or (int(masks[i]) >> k) & 1:
+                kept.add((r[0] + k % w, r[2] + k // w))
+        kept_total += len(kept)
+        rect_total += w * h
+        ex, ey = math.sqrt(a), math.sqrt(c)
+        x0, x1 = max(0, int(math.floor(mx - ex - 1))), min(cam.width - 1, int(math.ceil(mx + ex + 1)))
+        y0, y1 = max(0, int(math.floor(my - ey - 1))), min(cam.height - 1, int(math.ceil(my + ey + 1)))
+        if x0 <= x1 and y0 <= y1:
+            ys, xs = np.mgrid[y0:y1 + 1, x0:x1 + 1]
+            dx, dy = xs + 0.5 - mx, ys + 0.5 - my
+            inside = (Q[0] * dx * dx + 2 * Q[1] * dx * dy + Q[2] * dy * dy) < 1.0
+            need = set(zip((xs[inside] // tw).tolist(), (ys[inside] // th).tolist()))
+            assert need <= kept, (i, need - kept)
+            checked += bool(need)
+        if not full:
+            e = 1.0 / 32
+            for (tx, ty) in kept:
+                X0, X1 = tx * tw + 0.5 - e, min(tx * tw + tw - 1, cam.width - 1) + 0.5 + e
+                Y0, Y1 = ty * th + 0.5 - e, min(ty * th + th - 1, cam.height - 1) + 0.5 + e
+                assert _min_r2_on_rect(Q, mx, my, X0, X1, Y0, Y1) < 1.002, (i, tx, ty)
+    return checked, kept_total, rect_total
+
+
+@pytest.mark.parametrize("cfg,n,tile", [(1, 4096, (16, 16)), (2, 20_000, (16, 8)), (3, 20_000, (16, 8)),
+                                        (3, 20_000, (8, 8)), (3, 20_000, (32, 16))])
+def test_rule_b2_tiles_conservative_and_tight(cfg, n, tile):
+    """Rule B2 keeps exactly the tiles of the rule-B1 rectangle the support
+    ellipse reaches (Sec. 3.1, Eq. 2: zero contribution outside r^2 < 1):
+    none that a pixel with FP64 r^2 < 1 needs is dropped, and each kept one
+    lies within the rule's inflation of the ellipse.  On the sheet scenes it
+    drops a few percent of the rectangle's tiles."""
+    sc = scenes.config_scene(cfg, n=n)
+    checked, kept, total = _check_b2(sc.planes, sc.n, sc.n_lobes, sc.cameras[0], *tile)
+    assert checked > n // 8
+    if cfg == 3:
+        assert kept < 0.97 * total
+
+
+def test_rule_b2_thin_rotated_huge_and_blurred_splats():
+    """Edge cases of rule B2 against FP64: thin sheets at many in-plane
+    angles and tilts (the x-range of a band comes from the rightmost or
+    leftmost point, or from the band's ends, on either side), splats larger
+    than the image, splats cut by every image edge, and a 2D blur."""
+    rng = np.random.default_rng(8)
+    prims = []
+    for k in range(120):
+        ang = rng.uniform(0, 2 * math.pi)
+        tilt = rng.uniform(-1.4, 1.4)
+        q = helpers_quat(ang, tilt)
+        s = (rng.uniform(0.05, 0.4), rng.uniform(0.003, 0.02), rng.uniform(0.05, 0.4))
+        mu = (rng.uniform(-1.4, 1.4), rng.uniform(-1.0, 1.0), rng.uniform(3.0, 6.0))
+        prims.append(prim(mu=mu, scale=s, quat=q, opacity=0.5))
+    prims.append(prim(mu=(0.0, 0.0, 1.0), scale=(2.0, 0.3, 0.2), opacity=0.5))     # wider than the image
+    prims.append(prim(mu=(0.3, 0.2, 2.0), scale=(0.01, 1.5, 0.01), opacity=0.5))   # taller than the image
+    P = planes_of(prims)
+    n = len(prims)
+    cam = scenes.pinhole(np.eye(3, dtype=np.float32), np.zeros(3, np.float32), 173, 131)
+    for tw, th in ((16, 16), (16, 8), (8, 8)):
+        for blur in (0.0, 0.3):
+            checked, kept, total = _check_b2(P, n, 0, cam, tw, th, blur=blur)
+            assert checked > n // 2 and kept < total
+
+
+def helpers_quat(ang, tilt):
+    """Quaternion of a rotation by `tilt` about x followed by `ang` about z."""
+    qa = axis_angle_quat((0.0, 0.0, 1.0), ang)
+    qt = axis_angle_quat((1.0, 0.0, 0.0), tilt)
+    w1, x1, y1, z1 = qa
+    w2, x2, y2, z2 = qt
+    return (w1 * w2 - x1 * x2 - y1 * y2 - z1 * z2, w1 * x2 + x1 * w2 + y1 * z2 - z1 * y2,
+            w1 * y2 - x1 * z2 + y1 * w2 + z1 * x2, w1 * z2 + x1 * y2 - y1 * x2 + z1 * w2)
+
+
 def test_bin_pairs_sorted_and_complete():
     sc = scenes.config_scene(1, n=1500)
     tiles, recs, ranges = oracle.bin_pairs(sc.planes, sc.n, sc.n_lobes, sc.cameras)
     assert np.all(np.diff(tiles.astype(np.int64)) >= 0)
-    rects, keys, binned = oracle.rule_rects(sc.planes, sc.n, sc.n_lobes, sc.cameras[0])
-    cnt = ((rects[:, 1] - rects[:, 0] + 1) * (rects[:, 3] - rects[:, 2] + 1))[binned > 0].sum()
+    rects, keys, binned, masks = oracle.rule_rects(sc.planes, sc.n, sc.n_lobes, sc.cameras[0], with_tiles=True)
+    area = (rects[:, 1] - rects[:, 0] + 1) * (rects[:, 3] - rects[:, 2] + 1)
+    bits = np.array([bin(int(m)).count("1") for m in masks])
+    cnt = np.where(area > 32, area, bits)[binned > 0].sum()
     assert len(tiles) == cnt
     for g in range(len(ranges) - 1):
         seg = recs[ranges[g]:ranges[g + 1]]
