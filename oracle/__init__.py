@@ -194,8 +194,8 @@ def rule_rects(planes, n, n_lobes, cam, blur_eps=0.0, tile_w=16, tile_h=16, b_lo
                with_tiles=False):
     """Rule B1 rectangles (n,4) = (tx0, tx1, ty0, ty1), rule D keys (n,), binned flags (n,),
     and with with_tiles the rule B2 tile masks (n,) of the rectangles (bit r w + q for tile
-    (tx0 + q, ty0 + r); 0xFFFFFFFF: every tile).  Primitives with b outside [b_lo, b_hi)
-    are not binned (geometry decomposition)."""
+    (tx0 + q, ty0 + r); 0xFFFFFFFF for rectangles of more than 32 tiles: every tile).
+    Primitives with b outside [b_lo, b_hi) are not binned (geometry decomposition)."""
     L = lib()
     p = np.ascontiguousarray(planes, dtype=np.float32)
     rects = np.zeros((max(n, 1), 4), np.int32)

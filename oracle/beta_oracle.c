@@ -390,16 +390,21 @@ static float rule_dop(float a, float b, float c, float d) {
  * Sigma' = [[a, b], [b, c]] with a = sxx, c = syy (blur included),
  * b = M0 . M1 and det = |M0 x M1|^2 + blur (a + c - blur), minors by Kahan's
  * algorithm; at height y (from the centre) the boundary is
- *   x = (b / c) y +- sqrt(K2 (det / c) max(0, 1 - y^2 / (K2 c))),  K2 = INFL^2.
- * Every operation is fp32, rounded to nearest, in the order written.  Returns
- * the tiles as bit r w + q for tile (tx0 + q, ty0 + r) of a w x h rectangle,
- * or 0xFFFFFFFF (every tile) when w h > 32 or the ellipse is degenerate. */
+ *   x = (b / c) y +- sqrt(K2 (det / c) max(0, 1 - y^2 (1 / (K2 c)))),  K2 = INFL^2.
+ * Every operation is fp32, rounded to nearest, in the order written.  The
+ * rule applies to rectangles of at least 2 x 2 and at most 32 tiles (a
+ * rectangle one tile wide or high loses a tile only where an image edge cuts
+ * the ellipse); the others, and degenerate ellipses, keep every tile.
+ * Returns the tiles as bit r w + q for tile (tx0 + q, ty0 + r) of a w x h
+ * rectangle (w h <= 32), 0xFFFFFFFF for larger rectangles. */
 static uint32_t rule_tiles(const float M0[3], const float M1[3], float sxx, float syy, float blur,
                            float pxc, float pyc, const int32_t rect[4], int32_t width, int32_t height,
                            int32_t tile_w, int32_t tile_h) {
   const int32_t w = rect[1] - rect[0] + 1, h = rect[3] - rect[2] + 1;
   if (w * h > 32) return 0xFFFFFFFFu;
-  if (!(sxx > 0.0f && syy > 0.0f)) return 0xFFFFFFFFu;
+  const uint32_t all = w * h == 32 ? 0xFFFFFFFFu : ((1u << (w * h)) - 1u);
+  if (w < 2 || h < 2) return all;
+  if (!(sxx > 0.0f && syy > 0.0f)) return all;
   const float INFL = 1.000244140625f; /* 1 + 2^-12 */
   const float PAD = 0.015625f;        /* 2^-6 pixel */
   float b = M0[0] * M1[0];
@@ -420,7 +425,8 @@ static uint32_t rule_tiles(const float M0[3], const float M1[3], float sxx, floa
   float K2 = INFL * INFL;
   float hh = (det / syy) * K2;
   float cc = syy * K2;
-  if (!(isfinite(ystar) && isfinite(slope) && isfinite(hh) && isfinite(cc) && cc > 0.0f)) return 0xFFFFFFFFu;
+  float icc = 1.0f / cc;
+  if (!(isfinite(ystar) && isfinite(slope) && isfinite(hh) && isfinite(icc) && cc > 0.0f)) return all;
   uint32_t mask = 0u;
   for (int32_t r = 0; r < h; ++r) {
     int32_t y0 = (rect[2] + r) * tile_h;
@@ -439,14 +445,14 @@ static uint32_t rule_tiles(const float M0[3], const float M1[3], float sxx, floa
     if (in_r) {
       xmax = xfull;
     } else {
-      float t = 1.0f - (yr * yr) / cc;
+      float t = 1.0f - (yr * yr) * icc;
       if (t < 0.0f) t = 0.0f;
       xmax = slope * yr + sqrtf(hh * t);
     }
     if (in_l) {
       xmin = -xfull;
     } else {
-      float t = 1.0f - (yl * yl) / cc;
+      float t = 1.0f - (yl * yl) * icc;
       if (t < 0.0f) t = 0.0f;
       xmin = slope * yl - sqrtf(hh * t);
     }
