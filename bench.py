@@ -166,15 +166,16 @@ def ncu_metric(kernel: str, name: str):
 
 
 REC_BYTES = 48          # raster record read per (tile, Beta) pair
-PROJ_BYTES = 60         # record + tile rectangle + depth key written per (view, Beta)
+PROJ_BYTES = 64         # record + tile rectangle + depth key + tile mask written per (view, Beta)
 GRAD2D_BYTES = 48       # 2D-gradient slot per (view, Beta)
 
 
 def hbm_roofline(stage_ms, ms_step, n, param_bytes, n_rec, K, px, peak, peak_src):
     """Algorithmic bytes of every stage (each stream counted once) over its
     CUDA-event time, against the measured HBM copy bandwidth:
-      project      params read + records written         n P + n_rec 60
-      bin_sort     rectangles twice + keys per record,   n_rec 20 + K 20
+      project      params read + records written         n P + n_rec 64
+      bin_sort     rectangles and tile masks twice,      n_rec 28 + K 20
+                   keys once per record,
                    item written + read + id written per pair
       raster_fwd   record + list index per pair, colour, K 52 + px (20 + 12 + 12)
                    T, n_contrib written, target read, dL/dC written
@@ -183,7 +184,7 @@ def hbm_roofline(stage_ms, ms_step, n, param_bytes, n_rec, K, px, peak, peak_src
       project_bwd  2D-gradient slots read and cleared,   n_rec 96 + 2 n P
                    params read, gradients written"""
     b = {"project": n * param_bytes + n_rec * PROJ_BYTES,
-         "bin_sort": n_rec * 20 + K * 20,
+         "bin_sort": n_rec * 28 + K * 20,
          "raster_fwd": K * (REC_BYTES + 4) + px * (20 + 12 + 12),
          "raster_bwd": K * (REC_BYTES + 4) + px * 20 + n_rec * GRAD2D_BYTES,
          "project_bwd": n_rec * 2 * GRAD2D_BYTES + 2 * n * param_bytes}
@@ -399,8 +400,8 @@ def main():
                 "algorithmic": f"{fl} flop x {evals:.4g} (pixel, Beta) evaluations inside the support (ellipse areas)"}
     else:
         nrec = V * sc.n
-        bytes_alg = {"project": sc.n * n_planes * 4 + nrec * 60,
-                     "bin_sort": nrec * 20 + K * 20,
+        bytes_alg = {"project": sc.n * n_planes * 4 + nrec * PROJ_BYTES,
+                     "bin_sort": nrec * 28 + K * 20,
                      "l1": rast.total_pixels * 3 * 4 * 3,
                      "project_bwd": nrec * 48 * 2 + sc.n * n_planes * 8}.get(dom, 0)
         achieved = bytes_alg / (stage_ms[dom] * 1e-3) / 1e9
@@ -625,7 +626,7 @@ def main():
                                                               for c, v in tune_ms.items()}},
                    "n_betas": sc.n, "views_per_gpu": V, "resolution": scenes.describe_sizes(cams),
                    "pairs_per_step": K, "l2": f"inputs larger than L2: {sc.n * n_planes * 4 / 1e6:.0f} MB params + "
-                                               f"{V * sc.pitch * 60 / 1e6:.0f} MB records per step",
+                                               f"{V * sc.pitch * 64 / 1e6:.0f} MB records per step",
                    "parallelism": f"dp{world} over views"},
         "ms_per_view": ms_step / V,
         "stage_ms": stage_ms,

@@ -121,8 +121,11 @@ int beta_debug_scan_faults(int32_t spin_limit, int64_t withhold_block);
 
 /* ---- sizes (host-only queries, no device work) ------------------------ */
 
-/* Bytes of the projection buffer `proj` for V views: 60 bytes per record
- * (48-byte raster record, 8-byte tile rectangle, 4-byte depth key). */
+/* Bytes of the projection buffer `proj` for V views: 64 bytes per record
+ * (48-byte raster record, 8-byte tile rectangle, 4-byte depth key, 4-byte
+ * mask of the rectangle's tiles the support reaches), then a worklist of
+ * 4 x V bytes per primitive (pitch rounded up to a multiple of 256) and one
+ * 4-byte count per 256 primitives, rounded up to 16 bytes. */
 size_t beta_proj_bytes(int32_t pitch, int32_t n_views);
 /* Total tiles of a batch of views (the length of tile_ranges is this + 1). */
 int64_t beta_total_tiles(const beta_camera* cams /* host */, int32_t n_views, const beta_opts* opt);
@@ -143,14 +146,16 @@ size_t beta_l1_workspace_bytes(const beta_camera* cams /* host */, int32_t n_vie
 
 /* Step 1 (Sec. 3.2, Sec. 3.3): per (view, primitive) activations, EWA
  * projection Sigma' = J W R S S^T R^T W^T J^T, projected centre, Beta shape
- * beta = 4 e^b, spherical-Beta colour, tile rectangle and depth key.
+ * beta = 4 e^b, spherical-Beta colour, tile rectangle, the tiles of the
+ * rectangle that the support ellipse reaches (Sec. 3.1, Eq. 2) and depth key.
  * Writes `proj` (beta_proj_bytes(pitch, n_views) bytes, 16-byte aligned). */
 int beta_project(const beta_params* prm /* host */, const beta_camera* cams /* host [n_views] */,
                  int32_t n_views, const beta_opts* opt /* host */, void* proj,
                  beta_stream_t stream);
 
 /* Step 2 (Sec. 3.2: overlapping primitives are composited in depth order): forms one
- * (tile, record) pair per tile each record's rectangle touches, as per-tile
+ * (tile, record) pair per tile of each record's rectangle that its support
+ * ellipse reaches (the tile mask beta_project wrote), as per-tile
  * lists (atomic counts, their scan, atomic slots), sorts every list by its
  * unique (depth key, record index) items, and writes the per-tile ranges:
  * the pairs end up sorted by (global tile, depth key, primitive index).

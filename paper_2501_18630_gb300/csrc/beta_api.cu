@@ -168,7 +168,7 @@ int beta_debug_scan_faults(int32_t spin_limit, int64_t withhold_block) {
 
 size_t beta_proj_bytes(int32_t pitch, int32_t n_views) {
   if (pitch <= 0 || n_views <= 0) return 0;
-  return (size_t)pitch * n_views * (16 * kRecordF4 + 12);
+  return proj_bytes(pitch, n_views);
 }
 
 int64_t beta_total_tiles(const beta_camera* cams, int32_t n_views, const beta_opts* opt) {

@@ -119,6 +119,7 @@ struct ViewGeo {
   float iz, j00, j11, j02, j12;
   float M0[3], M1[3];        // M = J W Rq S (2 x 3)
   float sxx, syy;            // diagonal of Sigma' (blur included)
+  float pxc, pyc;            // projected centre (rule B1's fp32 value)
 };
 
 // Rule chain, view-independent part.  Returns false if the primitive is
@@ -208,6 +209,8 @@ __device__ __forceinline__ bool rule_view(const PrimGeo& pg, const ViewDev& V, f
   float ey = __fadd_rn(__fmul_rn(__fsqrt_rn(syy), INFL), PAD);
   float pxc = __fadd_rn(__fmul_rn(g.j00, g.tc[0]), V.cx);
   float pyc = __fadd_rn(__fmul_rn(g.j11, g.tc[1]), V.cy);
+  g.pxc = pxc;
+  g.pyc = pyc;
   float lox = __fsub_rn(__fsub_rn(pxc, ex), 0.5f), hix = __fsub_rn(__fadd_rn(pxc, ex), 0.5f);
   float loy = __fsub_rn(__fsub_rn(pyc, ey), 0.5f), hiy = __fsub_rn(__fadd_rn(pyc, ey), 0.5f);
   if (!(isfinite(lox) && isfinite(hix) && isfinite(loy) && isfinite(hiy))) return false;
@@ -225,6 +228,119 @@ __device__ __forceinline__ bool rule_view(const PrimGeo& pg, const ViewDev& V, f
   rect[2] = (int)j0 >> tile_shift_h;
   rect[3] = (int)j1 >> tile_shift_h;
   return true;
+}
+
+// a*b - c*d with Kahan's fused multiply-add algorithm (one rounding error)
+__device__ __forceinline__ float rule_dop(float a, float b, float c, float d) {
+  const float w = __fmul_rn(c, d);
+  const float e = __fmaf_rn(-c, d, w);
+  const float f = __fmaf_rn(a, b, -w);
+  return __fadd_rn(f, e);
+}
+
+// Rule B2: the tiles of the rule B1 rectangle that the support ellipse
+// reaches (Sec. 3.1, Eq. 2: the Beta kernel is exactly zero outside r^2 < 1).
+// For every tile row, the band of its pixel-centre rows (widened by PAD) is
+// cut with the ellipse of Sigma' inflated by INFL: its x-range over the band
+// is the whole half-width when the ellipse's rightmost (leftmost) point lies
+// in the band, else the boundary at the band end nearest that point,
+//   x = (b / c) y +- sqrt(K2 (det / c) max(0, 1 - y^2 (1 / (K2 c)))),  K2 = INFL^2,
+// with a = sxx, c = syy (blur included), b = M0 . M1 and
+// det = |M0 x M1|^2 + blur (a + c - blur) (minors by Kahan's algorithm).  The
+// columns whose centres lie in that range widened by PAD give the row's
+// tiles.  fp32, every operation rounded to nearest, in the order written (the
+// oracle implements the same written rule).  The rule applies to rectangles
+// of at least 2 x 2 and at most 32 tiles (one tile wide or high, a rectangle
+// loses a tile only where an image edge cuts the ellipse); the others, and
+// degenerate ellipses, keep every tile.  Returns the kept tiles as bit
+// r w + q for tile (tx0 + q, ty0 + r) of a w x h rectangle (w h <= 32),
+// 0xFFFFFFFF for larger rectangles.
+__device__ __forceinline__ uint32_t rule_all_tiles(const int rect[4]) {
+  const int wh = (rect[1] - rect[0] + 1) * (rect[3] - rect[2] + 1);
+  return wh >= 32 ? 0xFFFFFFFFu : (1u << wh) - 1u;
+}
+// Does rule B2 apply to the rectangle (at least 2 x 2 and at most 32 tiles)?
+__device__ __forceinline__ bool rule_tiles_apply(const int rect[4]) {
+  const int w = rect[1] - rect[0] + 1, h = rect[3] - rect[2] + 1;
+  return w >= 2 && h >= 2 && w * h <= 32;
+}
+__device__ __forceinline__ uint32_t rule_tiles(const ViewGeo& g, const ViewDev& V, float blur, int tile_shift_w,
+                                               int tile_h, const int rect[4]) {
+  const int w = rect[1] - rect[0] + 1, h = rect[3] - rect[2] + 1;
+  if (w * h > 32) return 0xFFFFFFFFu;
+  const uint32_t all = rule_all_tiles(rect);
+  if (w < 2 || h < 2) return all;
+  if (!(g.sxx > 0.0f && g.syy > 0.0f)) return all;
+  const float INFL = 1.000244140625f;  // 1 + 2^-12
+  const float PAD = 0.015625f;         // 2^-6 pixel
+  const float b = rn_dot3(g.M0[0], g.M1[0], g.M0[1], g.M1[1], g.M0[2], g.M1[2]);
+  const float m01 = rule_dop(g.M0[0], g.M1[1], g.M0[1], g.M1[0]);
+  const float m02 = rule_dop(g.M0[0], g.M1[2], g.M0[2], g.M1[0]);
+  const float m12 = rule_dop(g.M0[1], g.M1[2], g.M0[2], g.M1[1]);
+  float det = __fmul_rn(m01, m01);
+  det = __fadd_rn(det, __fmul_rn(m02, m02));
+  det = __fadd_rn(det, __fmul_rn(m12, m12));
+  det = __fadd_rn(det, __fmul_rn(blur, __fsub_rn(__fadd_rn(g.sxx, g.syy), blur)));
+  const float sa = __fsqrt_rn(g.sxx), sc = __fsqrt_rn(g.syy);
+  const float xfull = __fmul_rn(sa, INFL);
+  const float ytop = __fmul_rn(sc, INFL);
+  const float ystar = __fdiv_rn(__fmul_rn(b, INFL), sa);
+  const float slope = __fdiv_rn(b, g.syy);
+  const float K2 = __fmul_rn(INFL, INFL);
+  const float hh = __fmul_rn(__fdiv_rn(det, g.syy), K2);
+  const float cc = __fmul_rn(g.syy, K2);
+  const float icc = __fdiv_rn(1.0f, cc);
+  if (!(isfinite(ystar) && isfinite(slope) && isfinite(hh) && isfinite(icc) && cc > 0.0f)) return all;
+  uint32_t mask = 0u;
+  for (int r = 0; r < h; ++r) {
+    const int y0 = (rect[2] + r) * tile_h;
+    const int y1 = min(y0 + tile_h - 1, V.height - 1);
+    float ya = __fsub_rn(__fsub_rn(__fadd_rn((float)y0, 0.5f), PAD), g.pyc);
+    float yb = __fsub_rn(__fadd_rn(__fadd_rn((float)y1, 0.5f), PAD), g.pyc);
+    if (ya < -ytop) ya = -ytop;
+    if (yb > ytop) yb = ytop;
+    if (!(ya <= yb)) continue;
+    const bool in_r = (ya <= ystar) && (ystar <= yb);
+    const bool in_l = (ya <= -ystar) && (-ystar <= yb);
+    const float yr = ystar < ya ? ya : yb;     // band end nearest the rightmost point
+    const float yl = -ystar < ya ? ya : yb;    // band end nearest the leftmost point
+    float xmax, xmin;
+    if (in_r) {
+      xmax = xfull;
+    } else {
+      float t = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(yr, yr), icc));
+      if (t < 0.0f) t = 0.0f;
+      xmax = __fadd_rn(__fmul_rn(slope, yr), __fsqrt_rn(__fmul_rn(hh, t)));
+    }
+    if (in_l) {
+      xmin = -xfull;
+    } else {
+      float t = __fsub_rn(1.0f, __fmul_rn(__fmul_rn(yl, yl), icc));
+      if (t < 0.0f) t = 0.0f;
+      xmin = __fsub_rn(__fmul_rn(slope, yl), __fsqrt_rn(__fmul_rn(hh, t)));
+    }
+    const float lo = __fsub_rn(__fsub_rn(__fadd_rn(g.pxc, xmin), PAD), 0.5f);
+    const float hi = __fsub_rn(__fadd_rn(__fadd_rn(g.pxc, xmax), PAD), 0.5f);
+    uint32_t rowbits;
+    if (!(isfinite(lo) && isfinite(hi))) {
+      rowbits = w == 32 ? 0xFFFFFFFFu : ((1u << w) - 1u);
+    } else {
+      float i0 = __fadd_rn(floorf(lo), 1.0f), i1 = __fsub_rn(ceilf(hi), 1.0f);
+      if (i0 < 0.0f) i0 = 0.0f;
+      const float wm1 = (float)(V.width - 1);
+      if (i1 > wm1) i1 = wm1;
+      if (i0 > i1) continue;
+      int q0 = (int)i0 >> tile_shift_w, q1 = (int)i1 >> tile_shift_w;
+      q0 = max(q0, rect[0]);
+      q1 = min(q1, rect[1]);
+      if (q0 > q1) continue;
+      q0 -= rect[0];
+      q1 -= rect[0];
+      rowbits = ((2u << q1) - 1u) & ~((1u << q0) - 1u);
+    }
+    mask |= rowbits << (r * w);
+  }
+  return mask;
 }
 
 // ---------------------------------------------------------------------------
@@ -355,8 +471,15 @@ struct ProjBuffers {
   float4* rec;       // [V * pitch * 4]
   uint2* rect;       // [V * pitch]  (tx0 | tx1 << 16, ty0 | ty1 << 16), tx0 > tx1 if empty
   uint32_t* key;     // [V * pitch]  depth key, 0xFFFFFFFF if not binned
+  uint32_t* tiles;   // [V * pitch]  rule B2 tiles of the rectangle (bit r w + q; all ones: every tile)
+  uint32_t* work;    // records rule B2 applies to (k_tiles' worklist): projection block b owns
+                     // entries [b kProjRegion V, (b + 1) kProjRegion V), in arbitrary order
+  uint32_t* n_work;  // [projection blocks] entries of each block's region
 };
 
+constexpr int kProjRegion = 256;   // primitives per projection block (its worklist region)
+inline int64_t proj_blocks(int32_t pitch) { return (pitch + kProjRegion - 1) / kProjRegion; }
+size_t proj_bytes(int32_t pitch, int32_t n_views);
 ProjBuffers proj_layout(void* proj, int32_t pitch, int32_t n_views);
 
 cudaError_t launch_project(const float* planes, int n, int pitch, int n_lobes, const ViewTable& vt,

@@ -23,14 +23,27 @@
 
 namespace beta {
 
+// Layout of the projection buffer: records, rectangles, keys and tile masks
+// per (view, primitive), then the rule-B2 worklist (kProjRegion x V entries
+// per projection block) and one entry count per block.
 ProjBuffers proj_layout(void* proj, int32_t pitch, int32_t n_views) {
   ProjBuffers b;
   char* p = (char*)proj;
-  size_t nrec = (size_t)pitch * n_views;
+  const size_t nrec = (size_t)pitch * n_views;
+  const size_t nwork = (size_t)proj_blocks(pitch) * kProjRegion * n_views;
   b.rec = (float4*)p;
   b.rect = (uint2*)(p + nrec * 16 * kRecordF4);
   b.key = (uint32_t*)(p + nrec * (16 * kRecordF4 + 8));
+  b.tiles = (uint32_t*)(p + nrec * (16 * kRecordF4 + 12));
+  b.work = (uint32_t*)(p + nrec * (16 * kRecordF4 + 16));
+  b.n_work = (uint32_t*)(p + nrec * (16 * kRecordF4 + 16) + nwork * 4);
   return b;
+}
+
+size_t proj_bytes(int32_t pitch, int32_t n_views) {
+  const size_t nrec = (size_t)pitch * n_views;
+  const size_t nwork = (size_t)proj_blocks(pitch) * kProjRegion * n_views;
+  return nrec * (16 * kRecordF4 + 16) + nwork * 4 + ((size_t)proj_blocks(pitch) * 4 + 15) / 16 * 16;
 }
 
 namespace {
@@ -130,9 +143,10 @@ template <int M>
 __global__ void __launch_bounds__(kFwdThreads, kFwdBlocksPerSM) k_project(const float* __restrict__ planes, int n, int pitch,
                                                  ViewTable vt, RenderOpts ro,
                                                  float4* __restrict__ rec, uint2* __restrict__ rect,
-                                                 uint32_t* __restrict__ key) {
+                                                 uint32_t* __restrict__ key, uint32_t* __restrict__ tiles,
+                                                 uint32_t* __restrict__ work, uint32_t* __restrict__ n_work) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= pitch) return;
+  const bool live = i < pitch;   // threads past the pitch write nothing but join the warp's append
   float p[15 + 6 * M];
   bool ok = false;
   if (i < n) load_params<M>(planes, pitch, i, p, ok);
@@ -141,6 +155,7 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdBlocksPerSM) k_project(const 
   if (ok) ok = rule_prim(p, pg);
   PrimAttr<M> at;
   if (ok) prim_attr<M>(p, ro.color_mode, at);
+  uint64_t need = 0;   // views whose record rule B2 applies to
   for (int v = 0; v < vt.n_views; ++v) {
     const ViewDev& V = vt.v[v];
     const size_t r = (size_t)v * pitch + i;
@@ -190,10 +205,61 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdBlocksPerSM) k_project(const 
       rec[r * kRecordF4 + 2] = o2;
       rect[r] = make_uint2((uint32_t)rc[0] | ((uint32_t)rc[1] << 16), (uint32_t)rc[2] | ((uint32_t)rc[3] << 16));
       key[r] = kk;
-    } else {
+      tiles[r] = rule_all_tiles(rc);   // k_tiles narrows it where rule B2 applies
+    } else if (live) {
       rect[r] = make_uint2(1u, 1u);
       key[r] = 0xffffffffu;
+      tiles[r] = 0u;
     }
+    if (bin && rule_tiles_apply(rc)) need |= 1ull << v;
+  }
+  // the records rule B2 applies to go on k_tiles' worklist, in this block's
+  // region: one atomic per warp, after the view loop (every thread of the
+  // warp gets here: none returned early)
+  const int lane = threadIdx.x & 31;
+  const int cnt = __popcll(need);
+  int incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  if (total == 0) return;
+  uint32_t base = 0;
+  if (lane == 31) base = atomicAdd(&n_work[blockIdx.x], (uint32_t)total);
+  base = __shfl_sync(0xffffffffu, base, 31) + (uint32_t)(incl - cnt);
+  uint32_t* region = work + (size_t)blockIdx.x * kProjRegion * vt.n_views;
+  for (uint64_t m = need; m; m &= m - 1ull) region[base++] = (uint32_t)(__ffsll((long long)m) - 1) * (uint32_t)pitch + (uint32_t)i;
+}
+
+__global__ void k_proj_prep(uint32_t* n_work, int nb) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) n_work[b] = 0u;
+}
+
+// Rule B2 for the records on the worklist: the rule chain recomputed (the
+// same fp32 operations as k_project, so the same rectangle) and the tiles of
+// the rectangle the support reaches.  The worklist packs the records that
+// need it into full warps; CTA b takes projection block b's region.
+__global__ void __launch_bounds__(256) k_tiles(const float* __restrict__ planes, int pitch, ViewTable vt,
+                                               RenderOpts ro, const uint32_t* __restrict__ work,
+                                               const uint32_t* __restrict__ n_work, uint32_t* __restrict__ tiles) {
+  const uint32_t nw = n_work[blockIdx.x];
+  const uint32_t* region = work + (size_t)blockIdx.x * kProjRegion * vt.n_views;
+  const int sw = __ffs(ro.tile_w) - 1, sh = __ffs(ro.tile_h) - 1;
+  for (uint32_t k = threadIdx.x; k < nw; k += blockDim.x) {
+    const uint32_t r = region[k];
+    const int v = (int)(r / (uint32_t)pitch), i = (int)(r - (uint32_t)v * (uint32_t)pitch);
+    float p[10];
+#pragma unroll
+    for (int q = 0; q < 10; ++q) p[q] = planes[(size_t)q * pitch + i];
+    PrimGeo pg;
+    ViewGeo g;
+    uint32_t kk;
+    int rc[4];
+    const ViewDev& V = vt.v[v];
+    if (rule_prim(p, pg) && rule_depth(pg, V, g, kk) && rule_view(pg, V, ro.blur_eps, sw, sh, g, rc))
+      tiles[r] = rule_tiles(g, V, ro.blur_eps, sw, ro.tile_h, rc);
   }
 }
 
@@ -451,7 +517,11 @@ static cudaError_t launch_project_m(const float* planes, int n, int pitch, const
                                     const RenderOpts& ro, ProjBuffers pb, cudaStream_t s) {
   int grid = (pitch + kFwdThreads - 1) / kFwdThreads;
   if (grid < 1) return cudaSuccess;
-  k_project<M><<<grid, kFwdThreads, 0, s>>>(planes, n, pitch, vt, ro, pb.rec, pb.rect, pb.key);
+  static_assert(kFwdThreads == kProjRegion, "a projection block owns one worklist region");
+  k_proj_prep<<<(grid + 255) / 256, 256, 0, s>>>(pb.n_work, grid);
+  k_project<M><<<grid, kFwdThreads, 0, s>>>(planes, n, pitch, vt, ro, pb.rec, pb.rect, pb.key, pb.tiles,
+                                            pb.work, pb.n_work);
+  k_tiles<<<grid, 256, 0, s>>>(planes, pitch, vt, ro, pb.work, pb.n_work, pb.tiles);
   return cudaGetLastError();
 }
 

@@ -3,8 +3,9 @@
 // Sec. 3.2 of arXiv 2501.18630 composites the primitives that overlap a
 // pixel in order of their camera depth.  The pairs (global tile, record) are
 // built as per-tile lists and each list is sorted on its own:
-//   1. k_tile_count:   every record adds one to a counter of each tile its
-//                      rectangle touches (kSub counters per tile, chosen by
+//   1. k_tile_count:   every record adds one to a counter of each tile of its
+//                      rectangle that its support reaches (the rule B2 mask
+//                      of the projection; kSub counters per tile, chosen by
 //                      the record index, so that the atomics on a busy tile
 //                      spread over several addresses);
 //   2. k_tile_scan:    exclusive scan of the counters = the tile ranges (list
@@ -121,35 +122,70 @@ __global__ void k_sort_prep(uint32_t* cnt, int total_tiles, u64* look, int64_t n
   }
 }
 
-// Tile rectangle of a record: (tx0 | tx1 << 16, ty0 | ty1 << 16), inclusive;
-// empty (tx0 > tx1) for records that are not binned.
+// Tiles of a record: its rectangle (tx0 | tx1 << 16, ty0 | ty1 << 16),
+// inclusive, empty (tx0 > tx1) for records that are not binned, and the mask
+// of the rectangle's tiles that its support reaches (rule B2: bit dy w + dx;
+// rectangles of more than 32 tiles keep every tile).
 struct Rect {
-  int tx0, ty0, w, n;
+  int tx0, ty0, w, h, n;
+  bool full;
+  uint32_t mask;
 };
-__device__ __forceinline__ Rect rect_of(uint2 r) {
+__device__ __forceinline__ Rect rect_of(uint2 r, uint32_t mask) {
   Rect q;
   q.tx0 = (int)(r.x & 0xffffu);
   q.ty0 = (int)(r.y & 0xffffu);
   const int tx1 = (int)(r.x >> 16), ty1 = (int)(r.y >> 16);
   q.w = tx1 - q.tx0 + 1;
-  q.n = (tx1 < q.tx0 || ty1 < q.ty0) ? 0 : q.w * (ty1 - q.ty0 + 1);
+  q.h = ty1 - q.ty0 + 1;
+  const bool empty = tx1 < q.tx0 || ty1 < q.ty0;
+  q.full = !empty && q.w * q.h > 32;
+  q.mask = mask;
+  q.n = empty ? 0 : (q.full ? q.w * q.h : __popc(mask));
   return q;
 }
 
+// Walks the kept tiles of a masked rectangle (not `full`) row by row, without
+// divisions: next() gives the offset dy * ntx + dx of the next tile.
+struct TileWalk {
+  uint32_t mask, rowmask, rm;
+  int w, h, dy, ntx;
+  __device__ __forceinline__ TileWalk(const Rect& q, int ntx_) : mask(q.mask), w(q.w), h(q.h), dy(0), ntx(ntx_) {
+    rowmask = w >= 32 ? 0xffffffffu : (1u << w) - 1u;
+    rm = mask & rowmask;
+  }
+  __device__ __forceinline__ bool next(int& off) {
+    while (rm == 0u) {
+      if (++dy >= h) return false;
+      rm = (mask >> (dy * w)) & rowmask;
+    }
+    const int dx = __ffs(rm) - 1;
+    rm &= rm - 1u;
+    off = dy * ntx + dx;
+    return true;
+  }
+};
+
 // 1. pairs per tile
-__global__ void __launch_bounds__(kSortThreads) k_tile_count(const uint2* __restrict__ rects, int64_t n_items,
+__global__ void __launch_bounds__(kSortThreads) k_tile_count(const uint2* __restrict__ rects,
+                                                         const uint32_t* __restrict__ tiles, int64_t n_items,
                                                          int pitch, ViewTable vt, int total_tiles,
                                                          uint32_t* cnt) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_items;
        r += (int64_t)gridDim.x * blockDim.x) {
-    const Rect q = rect_of(rects[r]);
+    const Rect q = rect_of(rects[r], tiles[r]);
     if (q.n == 0) continue;
     const int v = (int)((uint32_t)r / (uint32_t)pitch);
     const int ntx = vt.v[v].ntx;
     uint32_t* c = cnt + (size_t)(r & (kSub - 1)) * crow(total_tiles) + vt.v[v].tile_off + q.ty0 * ntx + q.tx0;
-    const int h = q.n / q.w;
-    for (int dy = 0; dy < h; ++dy, c += ntx)
-      for (int dx = 0; dx < q.w; ++dx) atomicAdd(&c[dx], 1u);
+    if (q.full) {
+      for (int dy = 0; dy < q.h; ++dy, c += ntx)
+        for (int dx = 0; dx < q.w; ++dx) atomicAdd(&c[dx], 1u);
+    } else {
+      TileWalk it(q, ntx);
+      int off;
+      while (it.next(off)) atomicAdd(&c[off], 1u);
+    }
   }
 }
 
@@ -292,6 +328,7 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scan(const uint32_t* __re
 // 3. every record appends its item to the lists of its tiles; up to four
 // slots are claimed before the first store so that the atomics overlap.
 __global__ void __launch_bounds__(kSortThreads) k_tile_scatter(const uint2* __restrict__ rects,
+                                                           const uint32_t* __restrict__ tiles,
                                                            const uint32_t* __restrict__ keys,
                                                            int64_t n_items, int pitch, ViewTable vt,
                                                            int total_tiles, uint32_t* cursor,
@@ -300,29 +337,44 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_scatter(const uint2* __re
   if (*status != 0) return;   // capacity overflow (or a failed scan): no list is written
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_items;
        r += (int64_t)gridDim.x * blockDim.x) {
-    const Rect q = rect_of(rects[r]);
+    const Rect q = rect_of(rects[r], tiles[r]);
     if (q.n == 0) continue;
     const int v = (int)((uint32_t)r / (uint32_t)pitch);
     const int ntx = vt.v[v].ntx;
-    uint32_t* cur = cursor + (size_t)(r & (kSub - 1)) * crow(total_tiles) + vt.v[v].tile_off;
+    uint32_t* cur = cursor + (size_t)(r & (kSub - 1)) * crow(total_tiles) + vt.v[v].tile_off + q.ty0 * ntx + q.tx0;
     const u64 item = ((u64)keys[r] << 32) | (u64)(uint32_t)r;
-    int dx = 0, row = q.ty0 * ntx + q.tx0;   // tile j of the rectangle, row-major, walked incrementally
-    for (int j0 = 0; j0 < q.n; j0 += 4) {
-      uint32_t slot[4];
+    if (q.full) {
+      int dx = 0, row = 0;   // tile j of the rectangle, row-major, walked incrementally
+      for (int j0 = 0; j0 < q.n; j0 += 4) {
+        uint32_t slot[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        slot[u] = 0xffffffffu;
-        if (j0 + u < q.n) {
-          slot[u] = atomicAdd(&cur[row + dx], 1u);
-          if (++dx == q.w) {
-            dx = 0;
-            row += ntx;
+        for (int u = 0; u < 4; ++u) {
+          slot[u] = 0xffffffffu;
+          if (j0 + u < q.n) {
+            slot[u] = atomicAdd(&cur[row + dx], 1u);
+            if (++dx == q.w) {
+              dx = 0;
+              row += ntx;
+            }
           }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (j0 + u < q.n && (int64_t)slot[u] < cap) items[slot[u]] = item;
+        for (int u = 0; u < 4; ++u)
+          if (j0 + u < q.n && (int64_t)slot[u] < cap) items[slot[u]] = item;
+      }
+    } else {
+      TileWalk it(q, ntx);
+      for (int j0 = 0; j0 < q.n; j0 += 4) {
+        uint32_t slot[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          int off;
+          slot[u] = (j0 + u < q.n && it.next(off)) ? atomicAdd(&cur[off], 1u) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j0 + u < q.n && (int64_t)slot[u] < cap) items[slot[u]] = item;
+      }
     }
   }
 }
@@ -629,12 +681,12 @@ cudaError_t launch_bin_sort(const ViewTable& vt, int pitch, ProjBuffers pb, uint
 
   k_sort_prep<<<(unsigned)std::max<int64_t>(grid_p, 1), kSortThreads, 0, s>>>(w.cnt, total_tiles, w.look, nb_scan,
                                                                           w.counters, d_count, d_status);
-  k_tile_count<<<(unsigned)grid_r, kSortThreads, 0, s>>>(pb.rect, n_items, pitch, vt, total_tiles, w.cnt);
+  k_tile_count<<<(unsigned)grid_r, kSortThreads, 0, s>>>(pb.rect, pb.tiles, n_items, pitch, vt, total_tiles, w.cnt);
   k_tile_scan<<<(unsigned)nb_scan, kSortThreads, 0, s>>>(w.cnt, total_tiles, w.look, w.counters, ranges, w.cursor,
                                                      w.longl, cap, d_count, d_status, g_spin_limit.load(),
                                                      g_withhold.load());
-  k_tile_scatter<<<(unsigned)grid_r, kSortThreads, 0, s>>>(pb.rect, pb.key, n_items, pitch, vt, total_tiles, w.cursor, w.items,
-                                                       cap, d_status);
+  k_tile_scatter<<<(unsigned)grid_r, kSortThreads, 0, s>>>(pb.rect, pb.tiles, pb.key, n_items, pitch, vt, total_tiles,
+                                                       w.cursor, w.items, cap, d_status);
   k_tile_sort<<<(unsigned)(device_sm_count() * 3), kSortThreads, 0, s>>>(ranges, total_tiles, w.longl, w.counters, w.items,
                                                               w.tmp, pair_vals, d_status);
   return cudaGetLastError();

@@ -43,8 +43,9 @@ def rasterize(planes_np, n, n_lobes, cams, opts=None, cap=None, check=True):
     return rast, planes
 
 
-def proj_arrays(rast):
-    """(records (V,pitch,12) f32, rects (V,pitch,4) int, keys (V,pitch) u32) from the proj buffer."""
+def proj_arrays(rast, with_tiles=False):
+    """(records (V,pitch,12) f32, rects (V,pitch,4) int, keys (V,pitch) u32[, rule B2 tile
+    masks (V,pitch) u32]) from the proj buffer."""
     V, pitch = rast.V, rast.pitch
     raw = rast.proj.cpu().numpy()
     nrec = V * pitch
@@ -52,6 +53,8 @@ def proj_arrays(rast):
     rr = raw[nrec * 48:nrec * 56].view(np.uint32).reshape(V, pitch, 2)
     rects = np.stack([rr[..., 0] & 0xFFFF, rr[..., 0] >> 16, rr[..., 1] & 0xFFFF, rr[..., 1] >> 16], -1).astype(np.int64)
     keys = raw[nrec * 56:nrec * 60].view(np.uint32).reshape(V, pitch)
+    if with_tiles:
+        return rec, rects, keys, raw[nrec * 60:nrec * 64].view(np.uint32).reshape(V, pitch)
     return rec, rects, keys
 
 

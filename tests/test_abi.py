@@ -64,7 +64,8 @@ def test_host_queries(L):
     arr = _lib.make_cameras(cams)
     assert L.beta_total_tiles(arr, 2, ctypes.byref(o)) == 82 * 53 + 16 * 16
     assert L.beta_total_pixels(arr, 2) == 1297 * 840 + 256 * 256
-    assert L.beta_proj_bytes(1024, 3) == 1024 * 3 * 60
+    assert L.beta_proj_bytes(1024, 3) == 1024 * 3 * 68 + 16
+    assert L.beta_proj_bytes(1000, 2) == 1000 * 2 * 64 + 1024 * 2 * 4 + 16
     assert L.beta_grad2d_bytes(1024, 2) == 1024 * 2 * 48
     assert L.beta_binsort_workspace_bytes(1024, 2, 10000, arr, ctypes.byref(o)) > 0
     assert L.beta_l1_workspace_bytes(arr, 2) >= 4 * ((1297 * 840 + 255) // 256)

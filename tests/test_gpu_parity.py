@@ -27,15 +27,16 @@ def test_project_records_match_oracle(cfg, n, views):
     sc = scenes.config_scene(cfg, n=n)
     cams = [sc.cameras[v] for v in views]
     rast, _ = gc.rasterize(sc.planes, sc.n, sc.n_lobes, cams)
-    rec, rects, keys = gc.proj_arrays(rast)
+    rec, rects, keys, tiles = gc.proj_arrays(rast, with_tiles=True)
     for v, cam in enumerate(cams):
         pr = oracle.project(sc.planes, sc.n, sc.n_lobes, cam)
-        orects, okeys, obinned = oracle.rule_rects(sc.planes, sc.n, sc.n_lobes, cam)
+        orects, okeys, obinned, otiles = oracle.rule_rects(sc.planes, sc.n, sc.n_lobes, cam, with_tiles=True)
         binned = (rects[v, :n, 0] <= rects[v, :n, 1]) & (rects[v, :n, 2] <= rects[v, :n, 3])
         assert np.array_equal(binned, obinned > 0)
         b = np.nonzero(binned)[0]
         assert np.array_equal(rects[v, b], orects[b])
         assert np.array_equal(keys[v, b], okeys[b])
+        assert np.array_equal(tiles[v, b], otiles[b])          # rule B2, bit for bit
         assert np.all(keys[v, np.nonzero(~binned)[0]] == 0xFFFFFFFF)
         r = rec[v, b].astype(np.float64)
         mu2 = np.stack([r[:, 0] + 0.5 - r[:, 2], r[:, 1] + 0.5 - r[:, 3]], -1)
@@ -100,6 +101,19 @@ def test_bin_sort_ragged_sizes():
         sc = scenes.config_scene(1, n=n, seed=11)
         cam = scenes.pinhole(*scenes.look_at((0.0, 0.0, -3.0)), 37, 53)
         _check_bins(sc, [cam])
+
+
+@pytest.mark.parametrize("n,pitch", [(1001, 1004), (4097, 4100), (300, 300)])
+def test_bin_sort_pitch_not_a_multiple_of_the_warp(n, pitch):
+    """A pitch that is a multiple of 4 but not of 32 (the last projection warp
+    is partial): records, rule B2 tile masks and lists equal the oracle's."""
+    base = scenes.config_scene(3, n=n, seed=13)
+    planes = np.zeros((base.planes.shape[0], pitch), np.float32)
+    planes[:, :n] = base.planes[:, :n]
+    planes[6, n:] = 1.0
+    cams = [scenes.ring_camera(4.0, 15.0, 0.3, 333, 201), scenes.ring_camera(4.0, 15.0, 1.9, 150, 90)]
+    sc = scenes.Scene(planes=planes, n=n, n_lobes=base.n_lobes, cameras=cams, name="ragged pitch")
+    assert _check_bins(sc, cams) > 0
 
 
 def test_bin_sort_lists_longer_than_one_shared_memory_pass():
