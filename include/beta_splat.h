@@ -92,7 +92,7 @@ typedef struct {
 
 /* Render options (host struct).  beta_default_opts() fills the defaults. */
 typedef struct {
-  int32_t tile_w, tile_h; /* pixel tile: 8x8, 16x8, 16x16 (default) or 32x16   */
+  int32_t tile_w, tile_h; /* pixel tile: 8x4, 8x8, 16x8, 16x16 (default) or 32x16 */
   int32_t batch_s;        /* records staged per raster batch: 64, 128 or 256 */
   int32_t color_mode;     /* 0: c0 + lobes, 1: c0 only (diffuse), 2: lobes only (specular) */
   float t_eps;            /* stop before a primitive once T < t_eps (2^-19)   */

@@ -18,8 +18,8 @@ from .batched import BatchedStep
 
 # (tile_w, tile_h, batch_s, persistent)
 CANDIDATES = [
-    (16, 16, 256, False), (16, 16, 256, True), (16, 16, 128, True), (16, 8, 128, False),
-    (16, 8, 128, True), (16, 8, 64, False), (8, 8, 64, False), (32, 16, 256, True),
+    (16, 16, 256, False), (16, 16, 128, True), (16, 8, 128, False), (16, 8, 64, False),
+    (8, 8, 64, False), (8, 8, 128, False), (8, 4, 64, False),
 ]
 
 

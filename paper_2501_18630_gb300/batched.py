@@ -20,9 +20,13 @@ from .render import Rasterizer
 class BatchedStep:
     def __init__(self, planes: torch.Tensor, n: int, n_lobes: int, cameras, target: torch.Tensor,
                  opts: _lib.BetaOpts | None = None, persistent: bool = True, headroom: float = 1.15,
-                 hit_masks: bool = True):
+                 hit_masks: bool = True, graph_project_bwd: bool = True):
+        """graph_project_bwd=False leaves the projection backward out of the
+        captured graph, for project_bwd_reduced() to run it in chunks, each
+        chunk's gradient all-reduce overlapping the next chunk."""
         self.planes = planes
         self.target = target
+        self.graph_project_bwd = bool(graph_project_bwd)
         self.rast = Rasterizer(n, planes.shape[1], n_lobes, cameras, opts, device=planes.device,
                                persistent=persistent, hit_masks=hit_masks)
         self.grad = torch.zeros_like(planes)
@@ -45,13 +49,27 @@ class BatchedStep:
             r.schedule()
         r.raster_fwd_l1(self.planes, self.target)
         r.raster_bwd(self.planes, r.dL_dcolor)
-        r.project_bwd(self.planes, self.grad)
+        if self.graph_project_bwd:
+            r.project_bwd(self.planes, self.grad)
+
+    def project_bwd_reduced(self, chunk: int | None = None):
+        """Projection backward in chunks of primitives, each chunk's gradient
+        summed over the ranks by an asynchronous all-reduce that overlaps the
+        next chunks (after a step() captured with graph_project_bwd=False)."""
+        from .distributed import reduce_gradients_chunked
+        r = self.rast
+        chunk = chunk or max(4, (r.n + 7) // 8)
+        return reduce_gradients_chunked(self.grad, lambda c0, c1: r.project_bwd(self.planes, self.grad, c0, c1),
+                                        r.n, chunk)
 
     def capture(self):
         side = torch.cuda.Stream(device=self.planes.device)
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
             self.body()                       # warm-up outside the graph (lazy module loading)
+            if not self.graph_project_bwd:
+                # consume the warm-up's 2D-gradient sums (the projection backward clears them)
+                self.rast.project_bwd(self.planes, self.grad)
         torch.cuda.current_stream().wait_stream(side)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
@@ -72,6 +90,8 @@ class BatchedStep:
             self.rast._alloc_pairs(int(math.ceil(k * self.headroom)) + 65536)
             self.graph = None
             self.step()
+            if not self.graph_project_bwd:
+                self.project_bwd_reduced()
             st, k = self.rast.device_status()
         if st != _lib.BETA_OK:
             raise _lib.BetaError("batched step", st, _lib.load().beta_status_string(st).decode())

@@ -29,7 +29,8 @@ bool valid_params(const beta_params* p) {
 int check_opts(const beta_opts* o) {
   if (!o) return BETA_ERR_ARG;
   const int shape = o->tile_w * 1000 + o->tile_h;
-  if (shape != 8008 && shape != 16008 && shape != 16016 && shape != 32016) return BETA_ERR_UNSUPPORTED;
+  if (shape != 8004 && shape != 8008 && shape != 16008 && shape != 16016 && shape != 32016)
+    return BETA_ERR_UNSUPPORTED;
   if (o->batch_s != 64 && o->batch_s != 128 && o->batch_s != 256) return BETA_ERR_UNSUPPORTED;
   if (o->color_mode < 0 || o->color_mode > 2) return BETA_ERR_ARG;
   if (!(o->t_eps >= 0.0f && o->t_eps < 1.0f)) return BETA_ERR_ARG;

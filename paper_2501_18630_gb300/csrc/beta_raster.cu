@@ -179,6 +179,12 @@ __device__ __forceinline__ uint32_t* hit_tile(uint32_t* hm, size_t hm_words, uin
   return w0 + n <= hm_words ? hm + w0 : nullptr;
 }
 
+// Resident CTAs per SM asked of the register allocator for `threads` threads
+// per CTA and `per_sm` threads per SM, at most the 32 CTAs an SM holds.
+constexpr int min_blocks(int threads, int per_sm) {
+  return per_sm / threads < 32 ? per_sm / threads : 32;
+}
+
 // Tile assignment: CTA b renders tile b, or (persistent) tiles are taken from
 // the schedule's counter in its longest-first order.  Returns -1 when done.
 template <bool PERSIST>
@@ -205,7 +211,7 @@ __device__ __forceinline__ void leave(uint32_t* ctr) {
 }
 
 template <int TW, int TH, int S, bool PERSIST>
-__global__ void __launch_bounds__(TW * TH, 1536 / (TW * TH)) k_raster_fwd(ViewTable vt, RenderOpts ro,
+__global__ void __launch_bounds__(TW * TH, min_blocks(TW * TH, 1536)) k_raster_fwd(ViewTable vt, RenderOpts ro,
                                                        const float4* __restrict__ rec,
                                                        const uint32_t* __restrict__ vals,
                                                        const uint32_t* __restrict__ ranges,
@@ -453,7 +459,7 @@ __device__ __forceinline__ bool bwd_terms(float4 f0, float4 f1, float4 f2, float
 }
 
 template <int TW, int TH, int S, bool PERSIST>
-__global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts ro,
+__global__ void __launch_bounds__(TW * TH, min_blocks(TW * TH, 1280)) k_raster_bwd(ViewTable vt, RenderOpts ro,
                                                        const float4* __restrict__ rec,
                                                        const uint32_t* __restrict__ vals,
                                                        const uint32_t* __restrict__ ranges,
@@ -529,6 +535,10 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
       cp_async_commit();
     }
 
+    // hit masks of the next chunk (chunks are walked from the last down),
+    // loaded one chunk ahead so that their DRAM latency overlaps a chunk
+    uint32_t pf_mine = 0u, pf_wide = 0u;
+    int pf_chunk = -1;
     int buf = 0;
     for (int b = nb - 1; b >= 0; --b) {
       const int lo = b * S;
@@ -556,10 +566,23 @@ __global__ void __launch_bounds__(TW * TH) k_raster_bwd(ViewTable vt, RenderOpts
         // marked `wide`; the transpose gives every lane its own records
         uint32_t wide, mine;
         if (hslot) {
-          const uint32_t* slot = hslot + (size_t)((lo + c) >> 5) * (NT + NW);
-          mine = slot[tid];                              // the forward's pass 1
+          const int j = (lo + c) >> 5;
+          if (pf_chunk == j) {                           // the forward's pass 1
+            mine = pf_mine;
+            wide = pf_wide;
+          } else {
+            const uint32_t* slot = hslot + (size_t)j * (NT + NW);
+            mine = slot[tid];
+            wide = slot[NT + warp];
+          }
+          if (j >= 1) {
+            const uint32_t* nslot = hslot + (size_t)(j - 1) * (NT + NW);
+            pf_mine = nslot[tid];
+            pf_wide = nslot[NT + warp];
+            pf_chunk = j - 1;
+          }
           const int limw = (int)wmax - (lo + c);         // no lane of the warp reaches past wmax
-          wide = slot[NT + warp] & (limw >= 32 ? 0xffffffffu : (1u << limw) - 1u);
+          wide &= limw >= 32 ? 0xffffffffu : (1u << limw) - 1u;
         } else {
           const int idx = c + lane;
           const uint32_t cov = (idx < cnt && (uint32_t)(lo + idx) < wmax)
@@ -780,10 +803,15 @@ cudaError_t bwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* r
   return cudaGetLastError();
 }
 
-// (tile shape, batch) -> instantiation.  Supported: 8x8, 16x8, 16x16, 32x16
-// tiles; batches of 64, 128 or 256 records (at most 4 records per thread).
+// (tile shape, batch) -> instantiation.  Supported: 8x4 (one warp), 8x8,
+// 16x8, 16x16, 32x16 tiles; batches of 64, 128 or 256 records (at most 8
+// records per thread).
 #define BETA_TILE_DISPATCH(FN, ...)                                                 \
   switch (ro.tile_w * 1000 + ro.tile_h) {                                           \
+    case 8004:                                                                      \
+      if (ro.batch_s == 64) return FN<8, 4, 64>(__VA_ARGS__);                       \
+      if (ro.batch_s == 128) return FN<8, 4, 128>(__VA_ARGS__);                     \
+      return FN<8, 4, 256>(__VA_ARGS__);                                            \
     case 8008:                                                                      \
       if (ro.batch_s == 64) return FN<8, 8, 64>(__VA_ARGS__);                       \
       if (ro.batch_s == 128) return FN<8, 8, 128>(__VA_ARGS__);                     \

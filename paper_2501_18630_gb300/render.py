@@ -173,12 +173,20 @@ class Rasterizer:
             _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), hm, hb, _vp(self.T_final),
             _vp(self.n_contrib), _vp(dL_dcolor), _vp(self.grad2d), _vp(self.status), _stream()))
 
-    def project_bwd(self, planes, grad_planes):
-        prm = self.params(planes)
+    def project_bwd(self, planes, grad_planes, c0: int = 0, c1: int | None = None):
+        """Raw-parameter gradients of primitives [c0, c1) (all by default): the
+        same entry point on the primitive range, through pointers offset by c0
+        (parameters, their gradients and the 2D-gradient slots, whose record
+        index v * pitch + i keeps the full pitch)."""
         assert grad_planes.shape == planes.shape and grad_planes.is_contiguous()
+        c1 = self.n if c1 is None else c1
+        assert 0 <= c0 <= c1 <= self.n and c0 % 4 == 0
+        assert planes.is_cuda and planes.dtype == torch.float32 and planes.is_contiguous()
+        prm = _lib.make_params(c1 - c0, self.pitch, self.n_lobes, planes.data_ptr() + 4 * c0)
         _lib.check("beta_project_bwd", self.L.beta_project_bwd(
-            ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.grad2d),
-            _vp(grad_planes), _vp(self.status), _stream()))
+            ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts),
+            ctypes.c_void_p(self.grad2d.data_ptr() + 4 * 12 * c0),
+            ctypes.c_void_p(grad_planes.data_ptr() + 4 * c0), _vp(self.status), _stream()))
 
     # -- composite calls ---------------------------------------------------
     def device_status(self):

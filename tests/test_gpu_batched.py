@@ -13,7 +13,7 @@ from tests import gpu_common as gc
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(8, 8), (16, 8), (16, 16), (32, 16)]
+SHAPES = [(8, 4), (8, 8), (16, 8), (16, 16), (32, 16)]
 
 
 @pytest.mark.parametrize("tw,th", SHAPES)
@@ -201,3 +201,45 @@ def test_hit_masks_give_the_same_results(tw, th, bs, persist):
     for (c, t, n_, g) in out[1:]:
         assert torch.equal(c, c0) and torch.equal(t, t0) and torch.equal(n_, n0)
         assert np.max(np.abs(g - g0) / scale) < 1e-4
+
+
+def test_projection_backward_in_chunks_equals_whole():
+    """The projection backward over primitive ranges (pointers offset by the
+    range start, the full pitch kept) gives the whole call's gradients bit
+    for bit from the same 2D gradients; the batched step with the projection
+    backward run in chunks after the replay (the multi-GPU overlap path, one
+    rank here) matches the step with it inside the graph."""
+    sc = scenes.config_scene(3, n=50_003)
+    sc = scenes.Scene(planes=np.ascontiguousarray(sc.planes), n=50_003, n_lobes=sc.n_lobes, cameras=sc.cameras)
+    cams = [scenes.ring_camera(4.0, 15.0, 0.7, 320, 240), scenes.ring_camera(4.0, 15.0, 2.0, 200, 150)]
+    tgt = torch.from_numpy(np.concatenate([t.reshape(-1) for t in scenes.target_images(cams, seed=12)])).cuda()
+    gc.ensure_built()
+    planes = torch.from_numpy(sc.planes).cuda()
+    r = render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, cams)
+    r.forward(planes)
+    _, d = r.l1_loss(tgt)
+    r.raster_bwd(planes, d)
+    saved = r.grad2d.clone()
+    g_whole = torch.zeros_like(planes)
+    r.project_bwd(planes, g_whole)
+    r.grad2d.copy_(saved)
+    g_parts = torch.zeros_like(planes)
+    from paper_2501_18630_gb300 import distributed
+    for c0, c1 in distributed.chunk_ranges(sc.n, 7001):
+        r.project_bwd(planes, g_parts, c0, c1)
+    torch.cuda.synchronize()
+    assert torch.equal(g_whole, g_parts)
+    assert bool((r.grad2d == 0).all())                     # every consumed slot cleared
+    opts = _lib.default_opts(tile_w=16, tile_h=8, batch_s=128)
+    a = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, tgt, opts=opts, persistent=False)
+    a.step()
+    a.check()
+    b = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, tgt, opts=opts, persistent=False,
+                            graph_project_bwd=False)
+    b.step()
+    b.project_bwd_reduced(chunk=9000)
+    b.check()
+    torch.cuda.synchronize()
+    ga, gb = a.grad.cpu().numpy()[:, :sc.n], b.grad.cpu().numpy()[:, :sc.n]
+    scale = np.abs(ga).max(axis=1, keepdims=True) + 1e-30
+    assert np.max(np.abs(ga - gb) / scale) < 1e-4
