@@ -55,8 +55,9 @@ def parse():
     ap.add_argument("--cpu-pixels", type=int, default=16384)
     ap.add_argument("--workload", type=int, default=3, choices=[3, 4, 5],
                     help="scene recipe: 3 = 1M Betas (default), 4 = 3M Betas, 5 = 6M Betas")
-    ap.add_argument("--no-hit-masks", action="store_true",
-                    help="the raster backward recomputes its cover pass instead of reading the forward's")
+    ap.add_argument("--hit-masks", choices=["on", "off"], default="on",
+                    help="the forward keeps its cover pass for the backward (on), or the backward recomputes "
+                         "it (off)")
     ap.add_argument("--config", default=None,
                     help="pin the raster configuration instead of autotuning, e.g. 16x16/256/P (P persistent, G one CTA per tile)")
     return ap.parse_args()
@@ -304,9 +305,7 @@ def main():
 
     # ---- autotuned batched step, captured as one CUDA graph -----------------
     from paper_2501_18630_gb300 import autotune, batched
-    # the 6M-Beta 4K workload keeps no per-pixel state between the raster
-    # passes beyond T and n_contrib (its backward recomputes the cover pass)
-    hit_masks = args.workload != 5 and not args.no_hit_masks
+    hit_masks = args.hit_masks == "on"
     t_tune = time.perf_counter()
     if args.config:
         shape, bsz, mode = args.config.split("/")
