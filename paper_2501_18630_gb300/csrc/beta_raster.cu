@@ -424,7 +424,11 @@ __device__ __forceinline__ int warp_sum10_field(int lane) {
 //   G5 = (dL/dalpha) alpha,  G6 = G5 log2(1 - r^2),  G7..9 = alpha T dL/dC.
 // The forward's alpha is recomputed; T_k = T_{k+1} / (1 - alpha_k) and the
 // suffix colour GS (as g . S) are updated only where `act` holds and the
-// pixel lies inside the support (r^2 < 1); returns that condition.
+// pixel lies inside the support (r^2 < 1); returns that condition.  ZERO:
+// every term is exactly zero where the condition fails (t and the colour
+// weight are zeroed, 1 - r^2 is clamped so that no term is 0 * inf), for a
+// caller that sums the terms over the warp without selecting them.
+template <bool ZERO>
 __device__ __forceinline__ bool bwd_terms(float4 f0, float4 f1, float4 f2, float xf, float yf, float amax,
                                           bool act, float gx, float gy, float gz, float& T, float& GS,
                                           float G[kGrad2d]) {
@@ -432,7 +436,9 @@ __device__ __forceinline__ bool bwd_terms(float4 f0, float4 f1, float4 f2, float
   const float r2 = rec_r2(f0, f1, xf, yf, u, vv);
   act = act && r2 < 1.0f;
   const float beta = f1.w;
-  const float base = 1.0f - r2;
+  // ZERO: 1 - r^2 >= 2^-24 wherever r^2 < 1, so the clamp changes nothing
+  // there and keeps every term finite elsewhere
+  const float base = ZERO ? fmaxf(1.0f - r2, 5.9604645e-8f) : 1.0f - r2;
   const float lb = lg2_approx(base);
   const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
   const float a = fminf(a0, amax);
@@ -440,11 +446,11 @@ __device__ __forceinline__ bool bwd_terms(float4 f0, float4 f1, float4 f2, float
   const float Tk = T * inv;
   const float gc = fmaf(gx, f2.y, fmaf(gy, f2.z, gz * f2.w));
   const float dLa = fmaf(Tk, gc, -GS * inv);
-  const float wgt = a * Tk;
+  const float wgt = (!ZERO || act) ? a * Tk : 0.0f;
   G[7] = wgt * gx;
   G[8] = wgt * gy;
   G[9] = wgt * gz;
-  const float t = a0 < amax ? dLa * a0 : 0.0f;           // clamped alpha: no o/beta/r^2 gradient
+  const float t = (a0 < amax && (!ZERO || act)) ? dLa * a0 : 0.0f;   // clamped alpha: no o/beta/r^2 gradient
   const float kk = t * rcp_approx(base);
   G[0] = kk * u;
   G[1] = kk * vv;
@@ -606,7 +612,7 @@ __global__ void __launch_bounds__(TW * TH, min_blocks(TW * TH, 1280)) k_raster_b
             seg &= ~(1u << k);
             const int s = c + k;
             float G[kGrad2d];
-            if (!bwd_terms(s_rec[buf][s][0], s_rec[buf][s][1], s_rec[buf][s][2], xf, yf, amax, true, gx, gy, gz,
+            if (!bwd_terms<false>(s_rec[buf][s][0], s_rec[buf][s][1], s_rec[buf][s][2], xf, yf, amax, true, gx, gy, gz,
                            T, GS, G))
               continue;                                // outside the support (the cover is conservative)
             float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
@@ -620,10 +626,8 @@ __global__ void __launch_bounds__(TW * TH, min_blocks(TW * TH, 1280)) k_raster_b
           mine &= ~(1u << kb);
           const int s = c + kb;
           float G[kGrad2d];
-          const bool act = bwd_terms(s_rec[buf][s][0], s_rec[buf][s][1], s_rec[buf][s][2], xf, yf, amax, mine_kb,
-                                     gx, gy, gz, T, GS, G);
-#pragma unroll
-          for (int q = 0; q < kGrad2d; ++q) G[q] = act ? G[q] : 0.0f;
+          bwd_terms<true>(s_rec[buf][s][0], s_rec[buf][s][1], s_rec[buf][s][2], xf, yf, amax, mine_kb, gx, gy, gz, T,
+                          GS, G);                    // zero terms where this pixel is not covered
           const float tot = warp_sum10(G, lane);
           float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
           if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
