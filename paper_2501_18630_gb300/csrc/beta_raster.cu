@@ -642,6 +642,466 @@ __global__ void __launch_bounds__(TW * TH, min_blocks(TW * TH, 1280)) k_raster_b
 }
 
 // ---------------------------------------------------------------------------
+// Pixel-pair raster kernels: every lane owns two horizontally adjacent pixels.
+// Warp w of a tile owns a BW x BH block (16 x 4 in tiles at least 16 wide,
+// else 8 x 8); lane L owns pixels (2 pc, r) and (2 pc + 1, r) of it, with
+// pc = L mod PC, r = L / PC, PC = BW / 2 pair columns.  A record's cover mask
+// has one bit per pair (bit L: the record may cover either pixel of lane L),
+// and the lanes walk the union of their two pixels' records: one set of
+// shared-memory record loads and, in the backward, one set of gradient
+// atomics serve both pixels (neighbouring pixels share most records), and the
+// warp-wide reductions of records covering many lanes serve 64 pixels.
+// ---------------------------------------------------------------------------
+
+template <int TW>
+struct PairBlock {
+  static constexpr int BW = TW % 16 == 0 ? 16 : 8;   // block width in pixels
+  static constexpr int BH = 64 / BW;                 // block height
+  static constexpr int PC = BW / 2;                  // pair columns
+  static constexpr int WX = TW / BW;                 // blocks per tile row
+};
+
+// Pairs of the BW x BH block with first pixel (bxf, byf) whose two pixel
+// centres the record's support r^2 < 1 may reach: bit PC r + pc for row r,
+// pair column pc.  Per row the support is the interval of block_cover (same
+// closed form, margins and dy); the pairs are those holding a column of it.
+template <int BW>
+__device__ __forceinline__ uint32_t pair_cover(float4 f0, float4 f1, float bxf, float byf) {
+  constexpr int BH = 64 / BW, PC = BW / 2;
+  constexpr uint32_t kPcMask = (1u << PC) - 1u;
+  const float p = f1.x, q1 = f1.y, q2 = f1.z;
+  const float X0 = (bxf - f0.x) + f0.z;              // dx of the block's first column
+  const float A = fmaf(p, p, q2 * q2);
+  const float iA = rcp_approx(A);
+  const float A1 = A * 1.00001f;
+  const float sxc = q1 * q2 * iA;
+  const float pq = p * q1;
+  uint32_t m = 0u;
+#pragma unroll
+  for (int r = 0; r < BH; ++r) {
+    const float dy = ((byf + (float)r) - f0.y) + f0.w;
+    const float t = pq * dy;
+    const float disc = fmaf(-t, t, A1);
+    const float w = sqrt_approx(fmaxf(disc, 0.0f)) * iA;
+    const float xc = fmaf(-sxc, dy, -X0);              // interval centre, in columns of the block
+    const float e = fmaf(1e-5f, fabsf(xc) + w, 1e-3f);
+    const int ilo = ceil_small(fminf(fmaxf(xc - w - e, 0.0f), (float)BW));         // in [0, BW]
+    const int ihi = floor_small(fmaxf(fminf(xc + w + e, (float)(BW - 1)), -1.0f));  // in [-1, BW - 1]
+    const int plo = ilo >> 1, phi = ihi >> 1;                                        // phi = -1 for ihi = -1
+    const uint32_t row = (kPcMask >> (PC - 1 - phi)) & (kPcMask << plo);            // pairs plo .. phi
+    m |= (disc > 0.0f && ilo <= ihi ? row : 0u) << (PC * r);
+  }
+  return m;
+}
+
+// r^2 of a staged record at the lane's two pixel centres (xf, yf) and
+// (xf + 1, yf), with their whitened coordinates: each pixel's the values
+// rec_r2 gives it (the row term q1 dy is shared), so that every pixel
+// composites the same way whatever the tiling, and the forward and the
+// backward see the same values.
+__device__ __forceinline__ void rec_r2_pair(float4 f0, float4 f1, float xf, float yf, float& u0, float& v0,
+                                            float& u1, float& v1, float& r2a, float& r2b) {
+  const float dx0 = (xf - f0.x) + f0.z;
+  const float dx1 = ((xf + 1.0f) - f0.x) + f0.z;
+  const float dy = (yf - f0.y) + f0.w;
+  const float qy = f1.y * dy;
+  u0 = f1.x * dx0;
+  v0 = fmaf(f1.z, dx0, qy);
+  u1 = f1.x * dx1;
+  v1 = fmaf(f1.z, dx1, qy);
+  r2a = fmaf(u0, u0, v0 * v0);
+  r2b = fmaf(u1, u1, v1 * v1);
+}
+
+template <int TW, int TH, int S, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, 1024)) k_raster_fwd2(
+    ViewTable vt, RenderOpts ro, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ ranges, float* __restrict__ color, float* __restrict__ Tout,
+    uint32_t* __restrict__ ncontrib, const int32_t* __restrict__ status, uint32_t* ctr,
+    const uint32_t* __restrict__ order, const float* __restrict__ target, float* __restrict__ dLdC,
+    float* __restrict__ l1_partial, uint32_t* __restrict__ hm, size_t hm_words) {
+  using PB = PairBlock<TW>;
+  constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
+  static_assert(TH % PB::BH == 0 && NT % 32 == 0, "tile must hold whole pair blocks");
+  __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
+  __shared__ float s_l1[NW];
+  __shared__ float s_tgt[3][2 * NT];   // the pixels' targets, copied in while the tile composites
+  __shared__ int s_item;
+  if (*status != 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float t_eps = ro.t_eps, amax = ro.alpha_max;
+  for (int iter = 0;; ++iter) {
+    const int g = next_tile<PERSIST>(iter, vt.total_tiles, ctr, order, &s_item);
+    if (g < 0) break;
+    const int v = view_of_tile(vt, g);
+    const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
+    const int lt = g - vt.v[v].tile_off;
+    const int ty = lt / ntx, tx = lt - ty * ntx;
+    const int bx = tx * TW + (warp % PB::WX) * PB::BW, by = ty * TH + (warp / PB::WX) * PB::BH;
+    const int x = bx + 2 * (lane % PB::PC), y = by + lane / PB::PC;   // pixels (x, y), (x + 1, y)
+    const bool in0 = x < W && y < H, in1 = x + 1 < W && y < H;
+    const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
+    const uint32_t start = ranges[g], end = ranges[g + 1];
+    uint32_t* const hslot = hit_tile<NT>(hm, hm_words, start, end, g);
+    if (target) {
+      const int64_t HW = (int64_t)W * H;
+      const int64_t o = 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        if (in0) cp_async4(&s_tgt[ch][2 * tid], target + o + ch * HW);
+        if (in1) cp_async4(&s_tgt[ch][2 * tid + 1], target + o + 1 + ch * HW);
+      }
+    }
+
+    // batch 0 goes to buffer 0 now; the list entries of batch 1 are loaded
+    // ahead so that its copies can be issued without waiting on them
+    uint32_t rn[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int jj = tid + q * NT;
+      if (jj < S && start + jj < end) stage_record(s_rec[0][jj], rec, vals[start + jj]);
+      const uint32_t j1 = start + S + jj;
+      rn[q] = (jj < S && j1 < end) ? vals[j1] : 0u;
+    }
+    cp_async_commit();
+
+    float T0 = 1.0f, T1 = 1.0f, C00 = 0.0f, C01 = 0.0f, C02 = 0.0f, C10 = 0.0f, C11 = 0.0f, C12 = 0.0f;
+    uint32_t last0 = 0, last1 = 0;
+    bool done0 = !in0, done1 = !in1;
+    bool warp_done = __all_sync(0xffffffffu, done0 && done1);
+
+    int buf = 0;
+    for (uint32_t base = start; base < end; base += S) {
+      cp_async_wait_all();
+      if (!__syncthreads_or(!(done0 && done1))) break;
+      const uint32_t nb = base + S;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int jj = tid + q * NT;
+        if (jj < S && nb + jj < end) stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
+        const uint32_t j2 = nb + S + jj;
+        rn[q] = (jj < S && j2 < end) ? vals[j2] : 0u;
+      }
+      cp_async_commit();
+      const int cnt = (int)min((uint32_t)S, end - base);
+      for (int c = 0; c < cnt && !warp_done; c += 32) {
+        // pass 1: lane k finds the pairs of this warp's block that record
+        // c + k may cover; the transpose gives every lane its records
+        const int idx = c + lane;
+        const uint32_t cov =
+            idx < cnt ? pair_cover<PB::BW>(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
+        uint32_t mine = transpose32(cov, lane);
+        if (hslot) {
+          uint32_t* slot = hslot + (size_t)((base - start + c) >> 5) * (NT + NW);
+          const uint32_t wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
+          slot[tid] = mine;
+          if (lane == 0) slot[NT + warp] = wide;
+        }
+        if (done0 && done1) mine = 0u;
+        // pass 2: every lane composites its records in list order at both
+        // of its pixels
+        while (mine) {
+          const int k = __ffs(mine) - 1;
+          mine &= mine - 1;
+          const int s = c + k;
+          const float4 f0 = s_rec[buf][s][0];
+          const float4 f1 = s_rec[buf][s][1];
+          float u0, v0, u1, v1, r2a, r2b;
+          rec_r2_pair(f0, f1, xf, yf, u0, v0, u1, v1, r2a, r2b);
+          const bool h0 = !done0 && r2a < 1.0f, h1 = !done1 && r2b < 1.0f;
+          if (!(h0 || h1)) continue;                    // outside the support (the cover is conservative)
+          const float4 f2 = s_rec[buf][s][2];
+          const uint32_t pos = base - start + (uint32_t)s + 1u;
+          if (h0) {
+            const float a = fminf(ex2_approx(fmaf(f1.w, lg2_approx(1.0f - r2a), f2.x)), amax);
+            const float w = a * T0;
+            C00 = fmaf(w, f2.y, C00);
+            C01 = fmaf(w, f2.z, C01);
+            C02 = fmaf(w, f2.w, C02);
+            T0 = T0 * (1.0f - a);
+            last0 = pos;
+            done0 = T0 < t_eps;
+          }
+          if (h1) {
+            const float a = fminf(ex2_approx(fmaf(f1.w, lg2_approx(1.0f - r2b), f2.x)), amax);
+            const float w = a * T1;
+            C10 = fmaf(w, f2.y, C10);
+            C11 = fmaf(w, f2.z, C11);
+            C12 = fmaf(w, f2.w, C12);
+            T1 = T1 * (1.0f - a);
+            last1 = pos;
+            done1 = T1 < t_eps;
+          }
+          if (done0 && done1) mine = 0u;
+        }
+        warp_done = __all_sync(0xffffffffu, done0 && done1);
+      }
+      buf ^= 1;
+    }
+    cp_async_wait_all();   // no copy may still land in a buffer the next tile fills
+    float l1 = 0.0f;
+    {
+      const int64_t HW = (int64_t)W * H;
+      const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
+      const int64_t o = 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+      const float scale = 1.0f / (3.0f * (float)HW);
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        if (!(i == 0 ? in0 : in1)) continue;
+        const float T = i == 0 ? T0 : T1;
+        const float c[3] = {(i == 0 ? C00 : C10) + T * vt.v[v].bg[0], (i == 0 ? C01 : C11) + T * vt.v[v].bg[1],
+                            (i == 0 ? C02 : C12) + T * vt.v[v].bg[2]};
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) color[o + i + ch * HW] = c[ch];
+        Tout[pix + i] = T;
+        ncontrib[pix + i] = i == 0 ? last0 : last1;
+        if (target) {
+          // the per-pixel L1 term and its gradient, as beta_l1_loss computes them
+#pragma unroll
+          for (int ch = 0; ch < 3; ++ch) {
+            const float d = c[ch] - s_tgt[ch][2 * tid + i];   // landed: the copies were waited for above
+            l1 += fabsf(d);
+            dLdC[o + i + ch * HW] = d > 0.0f ? scale : (d < 0.0f ? -scale : 0.0f);
+          }
+        }
+      }
+    }
+    if (target) {
+      // tile partial sum of |C - target|, reduced in a fixed order
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+      if (lane == 0) s_l1[warp] = l1;
+      __syncthreads();
+      if (tid == 0) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) t += s_l1[w];
+        l1_partial[g] = t;
+      }
+      __syncthreads();
+    }
+  }
+  leave<PERSIST>(ctr);
+}
+
+// One pixel's terms (bwd_terms with ZERO) from its whitened coordinates,
+// added to G when ADD.
+template <bool ADD>
+__device__ __forceinline__ bool pix_terms(float u, float vv, float r2, float4 f1, float4 f2, float amax, bool act,
+                                          float gx, float gy, float gz, float& T, float& GS, float G[kGrad2d]) {
+  act = act && r2 < 1.0f;
+  const float beta = f1.w;
+  const float base = fmaxf(1.0f - r2, 5.9604645e-8f);   // 1 - r^2 >= 2^-24 wherever r^2 < 1
+  const float lb = lg2_approx(base);
+  const float a0 = ex2_approx(fmaf(beta, lb, f2.x));   // the forward's alpha
+  const float a = fminf(a0, amax);
+  const float inv = rcp_approx(1.0f - a);
+  const float Tk = T * inv;
+  const float gc = fmaf(gx, f2.y, fmaf(gy, f2.z, gz * f2.w));
+  const float dLa = fmaf(Tk, gc, -GS * inv);
+  const float wgt = act ? a * Tk : 0.0f;
+  const float t = (a0 < amax && act) ? dLa * a0 : 0.0f;   // clamped alpha: no o/beta/r^2 gradient
+  const float kk = t * rcp_approx(base);
+  const float g0 = kk * u, g1 = kk * vv;
+  const float H[kGrad2d] = {g0, g1, g0 * u, g0 * vv, g1 * vv, t, t * lb, wgt * gx, wgt * gy, wgt * gz};
+#pragma unroll
+  for (int q = 0; q < kGrad2d; ++q) G[q] = ADD ? G[q] + H[q] : H[q];
+  GS = act ? fmaf(wgt, gc, GS) : GS;
+  T = act ? Tk : T;
+  return act;
+}
+
+template <int TW, int TH, int S, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, 1024)) k_raster_bwd2(
+    ViewTable vt, RenderOpts ro, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ ranges, const float* __restrict__ Tfin, const uint32_t* __restrict__ ncontrib,
+    const float* __restrict__ dLdC, float* __restrict__ grad2d, const int32_t* __restrict__ status, uint32_t* ctr,
+    const uint32_t* __restrict__ order, const uint32_t* __restrict__ hm, size_t hm_words) {
+  using PB = PairBlock<TW>;
+  constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
+  static_assert(TH % PB::BH == 0 && NT % 32 == 0, "tile must hold whole pair blocks");
+  __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
+  __shared__ uint32_t s_ridx[2][S];
+  __shared__ uint32_t s_wmax[NW];
+  __shared__ int s_item;
+  if (*status != 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float amax = ro.alpha_max;
+  const int my_field = warp_sum10_field(lane);
+  for (int iter = 0;; ++iter) {
+    const int g = next_tile<PERSIST>(iter, vt.total_tiles, ctr, order, &s_item);
+    if (g < 0) break;
+    const int v = view_of_tile(vt, g);
+    const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
+    const int lt = g - vt.v[v].tile_off;
+    const int ty = lt / ntx, tx = lt - ty * ntx;
+    const int bx = tx * TW + (warp % PB::WX) * PB::BW, by = ty * TH + (warp / PB::WX) * PB::BH;
+    const int x = bx + 2 * (lane % PB::PC), y = by + lane / PB::PC;   // pixels (x, y), (x + 1, y)
+    const bool in0 = x < W && y < H, in1 = x + 1 < W && y < H;
+    const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
+    const uint32_t range0 = ranges[g];
+    const uint32_t* lst = vals + range0;
+    const uint32_t* const hslot = hit_tile<NT>(const_cast<uint32_t*>(hm), hm_words, range0, ranges[g + 1], g);
+
+    float T0 = 1.0f, T1 = 1.0f, GS0 = 0.0f, GS1 = 0.0f;
+    float g0x = 0.0f, g0y = 0.0f, g0z = 0.0f, g1x = 0.0f, g1y = 0.0f, g1z = 0.0f;
+    uint32_t nl0 = 0, nl1 = 0;
+    {
+      const int64_t HW = (int64_t)W * H;
+      const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
+      const float* gb = dLdC + 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+      const float* bg = vt.v[v].bg;
+      if (in0) {
+        g0x = gb[0];
+        g0y = gb[HW];
+        g0z = gb[2 * HW];
+        T0 = Tfin[pix];
+        nl0 = ncontrib[pix];
+        GS0 = T0 * (g0x * bg[0] + g0y * bg[1] + g0z * bg[2]);
+      }
+      if (in1) {
+        g1x = gb[1];
+        g1y = gb[HW + 1];
+        g1z = gb[2 * HW + 1];
+        T1 = Tfin[pix + 1];
+        nl1 = ncontrib[pix + 1];
+        GS1 = T1 * (g1x * bg[0] + g1y * bg[1] + g1z * bg[2]);
+      }
+    }
+    const uint32_t nlm = max(nl0, nl1);
+    const uint32_t wmax = __reduce_max_sync(0xffffffffu, nlm);
+    if (lane == 0) s_wmax[warp] = wmax;
+    __syncthreads();
+    int bmax = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) bmax = max(bmax, (int)s_wmax[w]);
+
+    // Batch b covers list positions [b S, min(b S + S, bmax)), b = nb - 1 .. 0
+    // (the forward's batches, so chunks start at multiples of 32).  The last
+    // goes to buffer 0 now; the list entries of the one before it are loaded
+    // ahead so that its copies issue without waiting.
+    const int nb = (bmax + S - 1) / S;
+    uint32_t rn[RPT];
+    {
+      const int lo0 = (nb - 1) * S, lo1 = lo0 - S;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int jj = tid + q * NT;
+        if (nb > 0 && jj < bmax - lo0) {
+          const uint32_t r = lst[lo0 + jj];
+          s_ridx[0][jj] = r;
+          stage_record(s_rec[0][jj], rec, r);
+        }
+        rn[q] = (lo1 >= 0 && jj < S) ? lst[lo1 + jj] : 0u;
+      }
+      cp_async_commit();
+    }
+
+    // hit masks of the next chunk (chunks are walked from the last down),
+    // loaded one chunk ahead so that their DRAM latency overlaps a chunk
+    uint32_t pf_mine = 0u, pf_wide = 0u;
+    int pf_chunk = -1;
+    int buf = 0;
+    for (int b = nb - 1; b >= 0; --b) {
+      const int lo = b * S;
+      const int cnt = min(S, bmax - lo);
+      cp_async_wait_all();
+      __syncthreads();
+      {
+        // copies of batch b - 1 (full) into the other buffer, entries of b - 2
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          const int jj = tid + q * NT;
+          if (b >= 1 && jj < S) {
+            s_ridx[buf ^ 1][jj] = rn[q];
+            stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
+          }
+          rn[q] = (b >= 2 && jj < S) ? lst[(b - 2) * S + jj] : 0u;
+        }
+        cp_async_commit();
+      }
+      for (int c = ((cnt - 1) >> 5) << 5; c >= 0; c -= 32) {
+        if ((uint32_t)(lo + c) >= wmax) continue;
+        uint32_t wide, mine;
+        if (hslot) {
+          const int j = (lo + c) >> 5;
+          if (pf_chunk == j) {                           // the forward's pass 1
+            mine = pf_mine;
+            wide = pf_wide;
+          } else {
+            const uint32_t* slot = hslot + (size_t)j * (NT + NW);
+            mine = slot[tid];
+            wide = slot[NT + warp];
+          }
+          if (j >= 1) {
+            const uint32_t* nslot = hslot + (size_t)(j - 1) * (NT + NW);
+            pf_mine = nslot[tid];
+            pf_wide = nslot[NT + warp];
+            pf_chunk = j - 1;
+          }
+          const int limw = (int)wmax - (lo + c);         // no lane of the warp reaches past wmax
+          wide &= limw >= 32 ? 0xffffffffu : (1u << limw) - 1u;
+        } else {
+          const int idx = c + lane;
+          const uint32_t cov = (idx < cnt && (uint32_t)(lo + idx) < wmax)
+                                   ? pair_cover<PB::BW>(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
+          wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
+          mine = transpose32(cov, lane);
+        }
+        const int lim = (int)nlm - (lo + c);           // only positions before a pixel's last contributor
+        mine &= lim >= 32 ? 0xffffffffu : (lim <= 0 ? 0u : (1u << lim) - 1u);
+        // pass 2, in reverse list order: between wide records every lane walks
+        // its own records at both of its pixels and adds their summed terms
+        // with three vector atomics; a wide record is done by the whole warp
+        // together (reduce-scatter, one atomic per value)
+        for (;;) {
+          const int kb = wide ? 31 - __clz(wide) : -1;                 // warp-uniform
+          const uint32_t above = kb >= 0 ? ~((2u << kb) - 1u) : 0xffffffffu;
+          uint32_t seg = mine & above;
+          mine &= ~above;
+          while (seg) {
+            const int k = 31 - __clz(seg);
+            seg &= ~(1u << k);
+            const int s = c + k;
+            const uint32_t pos = (uint32_t)(lo + s);
+            const float4 f0 = s_rec[buf][s][0], f1 = s_rec[buf][s][1], f2 = s_rec[buf][s][2];
+            float u0, v0, u1, v1, r2a, r2b;
+            rec_r2_pair(f0, f1, xf, yf, u0, v0, u1, v1, r2a, r2b);
+            float G[kGrad2d];
+            const bool a0 = pix_terms<false>(u0, v0, r2a, f1, f2, amax, pos < nl0, g0x, g0y, g0z, T0, GS0, G);
+            const bool a1 = pix_terms<true>(u1, v1, r2b, f1, f2, amax, pos < nl1, g1x, g1y, g1z, T1, GS1, G);
+            if (!(a0 || a1)) continue;                  // outside the support (the cover is conservative)
+            float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
+            red_add_v4(gdst + 0, G[0], G[1], G[2], G[3]);
+            red_add_v4(gdst + 4, G[4], G[5], G[6], G[7]);
+            red_add_v4(gdst + 8, G[8], G[9], 0.0f, 0.0f);
+          }
+          if (kb < 0) break;
+          wide &= ~(1u << kb);
+          const bool mine_kb = (mine >> kb) & 1u;
+          mine &= ~(1u << kb);
+          const int s = c + kb;
+          const uint32_t pos = (uint32_t)(lo + s);
+          const float4 f0 = s_rec[buf][s][0], f1 = s_rec[buf][s][1], f2 = s_rec[buf][s][2];
+          float u0, v0, u1, v1, r2a, r2b;
+          rec_r2_pair(f0, f1, xf, yf, u0, v0, u1, v1, r2a, r2b);
+          float G[kGrad2d];                              // zero where a pixel is not covered
+          pix_terms<false>(u0, v0, r2a, f1, f2, amax, mine_kb && pos < nl0, g0x, g0y, g0z, T0, GS0, G);
+          pix_terms<true>(u1, v1, r2b, f1, f2, amax, mine_kb && pos < nl1, g1x, g1y, g1z, T1, GS1, G);
+          const float tot = warp_sum10(G, lane);
+          float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
+          if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
+        }
+      }
+      buf ^= 1;
+    }
+    cp_async_wait_all();   // no copy may still land in a buffer the next tile fills
+    __syncthreads();
+  }
+  leave<PERSIST>(ctr);
+}
+
+// ---------------------------------------------------------------------------
 // longest-first schedule: bucket b = bit length of the tile's pair count,
 // buckets emitted from the longest down (order inside a bucket is arbitrary:
 // the result of a tile does not depend on when it runs).
@@ -763,6 +1223,12 @@ cudaError_t launch_schedule(const ViewTable& vt, const uint32_t* ranges, uint32_
 
 namespace {
 
+// Tiles that hold whole pixel-pair blocks (8 x 8 blocks in 8-wide tiles,
+// 16 x 4 in wider ones) use the pixel-pair kernels; 8 x 4 tiles use the
+// one-pixel-per-lane ones.
+template <int TW, int TH>
+constexpr bool kPairs = TH % PairBlock<TW>::BH == 0;
+
 template <typename K>
 int persistent_grid(K kernel, int threads, int total_tiles) {
   int per_sm = 0;
@@ -776,15 +1242,29 @@ cudaError_t fwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* r
                       const uint32_t* vals, const uint32_t* ranges, float* color, float* T_final,
                       uint32_t* n_contrib, const int32_t* status, uint32_t* sched, const float* target,
                       float* dL_dcolor, float* l1_partial, HitMasks hm, cudaStream_t s) {
-  if (sched) {
-    auto k = k_raster_fwd<TW, TH, S, true>;
-    k<<<persistent_grid(k, TW * TH, vt.total_tiles), TW * TH, 0, s>>>(
-        vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched + 0, sched + kSchedOrder,
-        target, dL_dcolor, l1_partial, hm.words, hm.n_words);
+  if constexpr (kPairs<TW, TH>) {
+    constexpr int NT = TW * TH / 2;
+    if (sched) {
+      auto k = k_raster_fwd2<TW, TH, S, true>;
+      k<<<persistent_grid(k, NT, vt.total_tiles), NT, 0, s>>>(
+          vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched + 0, sched + kSchedOrder,
+          target, dL_dcolor, l1_partial, hm.words, hm.n_words);
+    } else {
+      k_raster_fwd2<TW, TH, S, false><<<vt.total_tiles, NT, 0, s>>>(
+          vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, nullptr, nullptr, target, dL_dcolor,
+          l1_partial, hm.words, hm.n_words);
+    }
   } else {
-    k_raster_fwd<TW, TH, S, false><<<vt.total_tiles, TW * TH, 0, s>>>(
-        vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, nullptr, nullptr, target, dL_dcolor,
-        l1_partial, hm.words, hm.n_words);
+    if (sched) {
+      auto k = k_raster_fwd<TW, TH, S, true>;
+      k<<<persistent_grid(k, TW * TH, vt.total_tiles), TW * TH, 0, s>>>(
+          vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched + 0, sched + kSchedOrder,
+          target, dL_dcolor, l1_partial, hm.words, hm.n_words);
+    } else {
+      k_raster_fwd<TW, TH, S, false><<<vt.total_tiles, TW * TH, 0, s>>>(
+          vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, nullptr, nullptr, target, dL_dcolor,
+          l1_partial, hm.words, hm.n_words);
+    }
   }
   return cudaGetLastError();
 }
@@ -794,15 +1274,29 @@ cudaError_t bwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* r
                       const uint32_t* vals, const uint32_t* ranges, const float* T_final,
                       const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
                       const int32_t* status, uint32_t* sched, HitMasks hm, cudaStream_t s) {
-  if (sched) {
-    auto k = k_raster_bwd<TW, TH, S, true>;
-    k<<<persistent_grid(k, TW * TH, vt.total_tiles), TW * TH, 0, s>>>(
-        vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, sched + 2,
-        sched + kSchedOrder, hm.words, hm.n_words);
+  if constexpr (kPairs<TW, TH>) {
+    constexpr int NT = TW * TH / 2;
+    if (sched) {
+      auto k = k_raster_bwd2<TW, TH, S, true>;
+      k<<<persistent_grid(k, NT, vt.total_tiles), NT, 0, s>>>(
+          vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, sched + 2,
+          sched + kSchedOrder, hm.words, hm.n_words);
+    } else {
+      k_raster_bwd2<TW, TH, S, false><<<vt.total_tiles, NT, 0, s>>>(
+          vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, nullptr, nullptr,
+          hm.words, hm.n_words);
+    }
   } else {
-    k_raster_bwd<TW, TH, S, false><<<vt.total_tiles, TW * TH, 0, s>>>(
-        vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, nullptr, nullptr,
-        hm.words, hm.n_words);
+    if (sched) {
+      auto k = k_raster_bwd<TW, TH, S, true>;
+      k<<<persistent_grid(k, TW * TH, vt.total_tiles), TW * TH, 0, s>>>(
+          vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, sched + 2,
+          sched + kSchedOrder, hm.words, hm.n_words);
+    } else {
+      k_raster_bwd<TW, TH, S, false><<<vt.total_tiles, TW * TH, 0, s>>>(
+          vt, ro, rec, vals, ranges, T_final, n_contrib, dL_dcolor, grad2d, status, nullptr, nullptr,
+          hm.words, hm.n_words);
+    }
   }
   return cudaGetLastError();
 }
@@ -848,7 +1342,9 @@ cudaError_t launch_raster_fwd(const ViewTable& vt, const RenderOpts& ro, const f
 }
 
 size_t hit_mask_bytes(const ViewTable& vt, const RenderOpts& ro, int64_t cap) {
-  const int64_t nt = (int64_t)ro.tile_w * ro.tile_h;
+  // one word per lane (per pixel pair in the pixel-pair kernels) and one per warp
+  const bool pairs = ro.tile_h % (ro.tile_w % 16 == 0 ? 4 : 8) == 0;
+  const int64_t nt = (int64_t)ro.tile_w * ro.tile_h / (pairs ? 2 : 1);
   const int64_t slots = (std::max<int64_t>(cap, 0) >> 5) + vt.total_tiles + 1;
   return (size_t)slots * (size_t)(nt + nt / 32) * sizeof(uint32_t);
 }

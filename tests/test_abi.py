@@ -71,9 +71,17 @@ def test_host_queries(L):
     assert L.beta_l1_workspace_bytes(arr, 2) >= 4 * ((1297 * 840 + 255) // 256)
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert L.beta_status_string(code)
-    # hit masks: per 32 pairs of capacity and per tile, one word per tile pixel and per 8x4 block
+    # hit masks: per 32 pairs of capacity and per tile, one word per lane (a pixel pair in
+    # tiles of whole 16x4 / 8x8 pair blocks, a pixel in 8x4 tiles) and one per warp
     tiles = 82 * 53 + 16 * 16
-    assert L.beta_hit_mask_bytes(arr, 2, ctypes.byref(o), 10000) == ((10000 >> 5) + tiles + 1) * (256 + 8) * 4
+    assert L.beta_hit_mask_bytes(arr, 2, ctypes.byref(o), 10000) == ((10000 >> 5) + tiles + 1) * (128 + 4) * 4
+    o84 = _lib.default_opts(tile_w=8, tile_h=4)
+    tiles84 = 163 * 210 + 32 * 64
+    assert L.beta_total_tiles(arr, 2, ctypes.byref(o84)) == tiles84
+    assert L.beta_hit_mask_bytes(arr, 2, ctypes.byref(o84), 10000) == ((10000 >> 5) + tiles84 + 1) * (32 + 1) * 4
+    o88 = _lib.default_opts(tile_w=8, tile_h=8)
+    tiles88 = 163 * 105 + 32 * 32
+    assert L.beta_hit_mask_bytes(arr, 2, ctypes.byref(o88), 10000) == ((10000 >> 5) + tiles88 + 1) * (32 + 1) * 4
     assert L.beta_hit_mask_bytes(arr, 2, ctypes.byref(o), -1) == 0
 
 
