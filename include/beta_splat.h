@@ -218,10 +218,12 @@ int beta_schedule(const beta_camera* cams, int32_t n_views, const beta_opts* opt
 
 /* Bytes of the optional hit-mask buffer of beta_raster_fwd(_l1) and
  * beta_raster_bwd for a pair capacity: per tile and per 32 list positions,
- * one 32-bit word per pixel of the tile (which of the 32 primitives may cover
- * that pixel) and one per 8x4 pixel block (which cover more than 12 of its
- * pixels): ((pair_capacity >> 5) + total_tiles + 1) x (tile pixels x 33/32)
- * x 4 bytes.  0 for invalid arguments. */
+ * one 32-bit word per thread of the tile's raster CTA (which of the 32
+ * primitives may cover its pixels: a pair of horizontally adjacent pixels,
+ * or one pixel in 8x4 tiles) and one per warp (which cover more than 12 of
+ * its threads' pixels): ((pair_capacity >> 5) + total_tiles + 1) x
+ * (L x 33/32) x 4 bytes, L = tile pixels / 2 (tile pixels for 8x4 tiles).
+ * 0 for invalid arguments. */
 size_t beta_hit_mask_bytes(const beta_camera* cams /* host */, int32_t n_views, const beta_opts* opt,
                            int64_t pair_capacity);
 

@@ -7,10 +7,14 @@
 //   alpha = min(alpha_max, o (1 - r^2)^beta),  C += T alpha c,  T *= 1 - alpha,
 // stopping before a primitive once T < t_eps.
 //
-// Layout: one CTA per TW x TH tile, one pixel per thread; warp w owns an 8x4
-// pixel block.  Records of the tile's list are staged S at a time in shared
-// memory (double-buffered cp.async, one batch ahead).  Each warp walks the
-// staged records 32 at a time in two passes.  First, lane k works out which
+// Layout: one CTA per TW x TH tile.  In 8 x 4 tiles (k_raster_fwd /
+// k_raster_bwd) every thread owns one pixel and warp w an 8 x 4 block; in the
+// others (k_raster_fwd2 / k_raster_bwd2, below) every thread owns two
+// horizontally adjacent pixels and the warp a 16 x 4 or 8 x 8 block, "pixel"
+// reading "pixel pair" in what follows.  Records of the tile's list are
+// staged S at a time in shared memory (double-buffered cp.async, one batch
+// ahead).  Each warp walks the staged records 32 at a time in two passes.
+// First, lane k works out which
 // of the block's 32 pixel centres record k may cover (per pixel row the
 // support is an interval in x, solved in closed form and widened slightly),
 // and a 32 x 32 bit transpose across the warp turns these into, per lane, the
@@ -653,6 +657,12 @@ __global__ void __launch_bounds__(TW * TH, min_blocks(TW * TH, 1280)) k_raster_b
 // warp-wide reductions of records covering many lanes serve 64 pixels.
 // ---------------------------------------------------------------------------
 
+// Threads per SM asked of the register allocator for the pixel-pair kernels:
+// 1280 (48 registers) where the record buffers of 64-record batches leave
+// room for that many CTAs, 1024 (64 registers) for larger batches, whose
+// shared memory holds fewer CTAs anyway.
+constexpr int pair_threads_per_sm(int S) { return S <= 64 ? 1280 : 1024; }
+
 template <int TW>
 struct PairBlock {
   static constexpr int BW = TW % 16 == 0 ? 16 : 8;   // block width in pixels
@@ -714,7 +724,7 @@ __device__ __forceinline__ void rec_r2_pair(float4 f0, float4 f1, float xf, floa
 }
 
 template <int TW, int TH, int S, bool PERSIST>
-__global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, 1024)) k_raster_fwd2(
+__global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_threads_per_sm(S))) k_raster_fwd2(
     ViewTable vt, RenderOpts ro, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, float* __restrict__ color, float* __restrict__ Tout,
     uint32_t* __restrict__ ncontrib, const int32_t* __restrict__ status, uint32_t* ctr,
@@ -912,7 +922,7 @@ __device__ __forceinline__ bool pix_terms(float u, float vv, float r2, float4 f1
 }
 
 template <int TW, int TH, int S, bool PERSIST>
-__global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, 1024)) k_raster_bwd2(
+__global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_threads_per_sm(S))) k_raster_bwd2(
     ViewTable vt, RenderOpts ro, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
     const uint32_t* __restrict__ ranges, const float* __restrict__ Tfin, const uint32_t* __restrict__ ncontrib,
     const float* __restrict__ dLdC, float* __restrict__ grad2d, const int32_t* __restrict__ status, uint32_t* ctr,
