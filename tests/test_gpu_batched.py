@@ -60,10 +60,15 @@ def test_persistent_gradients_match_default():
     cams = [scenes.ring_camera(4.0, 15.0, 0.7, 320, 240)]
     tgt = torch.from_numpy(scenes.target_images(cams, seed=2)[0].reshape(-1)).cuda()
     grads = []
+    # the default 16x16 and every other tile shape but 8x4 run the pixel-pair
+    # kernels; 8x4 the one-pixel-per-lane ones, a direct cross-check of the two
     for opts, persist in ((None, False), (_lib.default_opts(tile_w=32, tile_h=16, batch_s=128), True),
                           (_lib.default_opts(tile_w=8, tile_h=8, batch_s=64), True),
                           (_lib.default_opts(tile_w=16, tile_h=8, batch_s=128), False),
-                          (_lib.default_opts(tile_w=16, tile_h=8, batch_s=128), True)):
+                          (_lib.default_opts(tile_w=16, tile_h=8, batch_s=128), True),
+                          (_lib.default_opts(tile_w=16, tile_h=8, batch_s=64), False),
+                          (_lib.default_opts(tile_w=8, tile_h=4, batch_s=64), False),
+                          (_lib.default_opts(tile_w=8, tile_h=4, batch_s=128), True)):
         gc.ensure_built()
         planes = torch.from_numpy(sc.planes).cuda()
         r = render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, cams, opts, persistent=persist)

@@ -52,7 +52,8 @@ def test_6m_betas_eight_4k_views_in_budget():
 
 def test_1m_betas_sixteen_views_benchmark_configuration():
     """The benchmark's own step: 1M Betas, 16 ring views of 1920x1080, 16x8
-    tiles, 128-record batches, one CTA per tile, captured and replayed.  Two
+    tiles, 64-record batches, one CTA per tile (the autotuner's pick, pixel-pair
+    raster kernels), captured and replayed.  Two
     views' binning equals the oracle's bit for bit (a view's lists are the
     view's own); sampled pixels of two views (including whole tiles) equal
     the FP64 oracle; the loss and gradients are finite."""
@@ -63,7 +64,7 @@ def test_1m_betas_sixteen_views_benchmark_configuration():
     planes = torch.from_numpy(sc.planes).cuda()
     tgt = torch.from_numpy(np.concatenate([t.reshape(-1) for t in scenes.target_images(cams, seed=77)])).cuda()
     step = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, tgt,
-                               opts=_lib.default_opts(tile_w=16, tile_h=8, batch_s=128), persistent=False)
+                               opts=_lib.default_opts(tile_w=16, tile_h=8, batch_s=64), persistent=False)
     step.step()
     k = step.check()
     torch.cuda.synchronize()
@@ -91,7 +92,7 @@ def _bench_step(sc, cams, tgt, persistent=False):
     gc.ensure_built()
     planes = torch.from_numpy(sc.planes).cuda()
     step = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, tgt,
-                               opts=_lib.default_opts(tile_w=16, tile_h=8, batch_s=128), persistent=persistent)
+                               opts=_lib.default_opts(tile_w=16, tile_h=8, batch_s=64), persistent=persistent)
     step.step()
     step.check()
     torch.cuda.synchronize()
@@ -99,7 +100,7 @@ def _bench_step(sc, cams, tgt, persistent=False):
 
 
 def test_1m_betas_benchmark_step_gradients_equal_per_view_default_path():
-    """The benchmark's captured step (16x8 tiles, 128-record batches, one CTA
+    """The benchmark's captured step (16x8 tiles, 64-record batches, one CTA
     per tile, 16 views at once) gives the same parameter gradients as the
     plain default path (16x16 tiles, 256-record batches) run one view at a
     time and summed: every primitive, every parameter, within 1e-4 of the
@@ -128,7 +129,7 @@ def test_1m_betas_benchmark_step_gradients_equal_per_view_default_path():
 
 def test_1m_betas_benchmark_step_gradients_match_finite_differences():
     """Gradients of the benchmark's captured step (1M Betas, 16 views of
-    1080p, 16x8 tiles, 128-record batches, one CTA per tile) for primitives
+    1080p, 16x8 tiles, 64-record batches, one CTA per tile) for primitives
     seen by several views, against central differences of the FP64 oracle's
     summed per-view L1 loss (each view on the sub-scene that can touch the
     primitive there): every parameter group within 1e-3."""
