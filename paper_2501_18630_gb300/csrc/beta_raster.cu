@@ -663,6 +663,11 @@ __global__ void __launch_bounds__(TW * TH, min_blocks(TW * TH, 1280)) k_raster_b
 // shared memory holds fewer CTAs anyway.
 constexpr int pair_threads_per_sm(int S) { return S <= 64 ? 1280 : 1024; }
 
+// Do TW x TH tiles hold whole pixel-pair blocks (16 x 4 in tiles at least
+// 16 wide, 8 x 8 in 8-wide ones)?  Those use the pixel-pair kernels, the
+// others (8 x 4) the one-pixel-per-lane ones; the hit-mask layout follows.
+constexpr bool pair_tiles(int tw, int th) { return th % (tw % 16 == 0 ? 4 : 8) == 0; }
+
 template <int TW>
 struct PairBlock {
   static constexpr int BW = TW % 16 == 0 ? 16 : 8;   // block width in pixels
@@ -732,7 +737,7 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
     float* __restrict__ l1_partial, uint32_t* __restrict__ hm, size_t hm_words) {
   using PB = PairBlock<TW>;
   constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
-  static_assert(TH % PB::BH == 0 && NT % 32 == 0, "tile must hold whole pair blocks");
+  static_assert(pair_tiles(TW, TH) && TH % PB::BH == 0 && NT % 32 == 0, "tile must hold whole pair blocks");
   __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
   __shared__ float s_l1[NW];
   __shared__ float s_tgt[3][2 * NT];   // the pixels' targets, copied in while the tile composites
@@ -929,7 +934,7 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
     const uint32_t* __restrict__ order, const uint32_t* __restrict__ hm, size_t hm_words) {
   using PB = PairBlock<TW>;
   constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
-  static_assert(TH % PB::BH == 0 && NT % 32 == 0, "tile must hold whole pair blocks");
+  static_assert(pair_tiles(TW, TH) && TH % PB::BH == 0 && NT % 32 == 0, "tile must hold whole pair blocks");
   __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
   __shared__ uint32_t s_ridx[2][S];
   __shared__ uint32_t s_wmax[NW];
@@ -1233,11 +1238,9 @@ cudaError_t launch_schedule(const ViewTable& vt, const uint32_t* ranges, uint32_
 
 namespace {
 
-// Tiles that hold whole pixel-pair blocks (8 x 8 blocks in 8-wide tiles,
-// 16 x 4 in wider ones) use the pixel-pair kernels; 8 x 4 tiles use the
-// one-pixel-per-lane ones.
 template <int TW, int TH>
-constexpr bool kPairs = TH % PairBlock<TW>::BH == 0;
+constexpr bool kPairs = pair_tiles(TW, TH);
+static_assert(pair_tiles(16, 8) && pair_tiles(8, 8) && !pair_tiles(8, 4), "pixel-pair tile rule");
 
 template <typename K>
 int persistent_grid(K kernel, int threads, int total_tiles) {
@@ -1353,7 +1356,7 @@ cudaError_t launch_raster_fwd(const ViewTable& vt, const RenderOpts& ro, const f
 
 size_t hit_mask_bytes(const ViewTable& vt, const RenderOpts& ro, int64_t cap) {
   // one word per lane (per pixel pair in the pixel-pair kernels) and one per warp
-  const bool pairs = ro.tile_h % (ro.tile_w % 16 == 0 ? 4 : 8) == 0;
+  const bool pairs = pair_tiles(ro.tile_w, ro.tile_h);
   const int64_t nt = (int64_t)ro.tile_w * ro.tile_h / (pairs ? 2 : 1);
   const int64_t slots = (std::max<int64_t>(cap, 0) >> 5) + vt.total_tiles + 1;
   return (size_t)slots * (size_t)(nt + nt / 32) * sizeof(uint32_t);
