@@ -37,8 +37,11 @@ UNIT = "Mpixel/s"
 FWD_FLOPS_PER_EVAL = 24   # r^2 (11), 1 - r^2, beta lg2 + log2 o, min, T alpha, C += (6), T update
 BWD_FLOPS_PER_EVAL = 60   # recompute alpha, T recovery, dL/dalpha, 10 gradient terms
 FP32_LANES_PER_SM = 128
-# raster_fwd includes the per-view L1 loss (computed in the forward's epilogue)
+# raster_fwd includes the per-view L1 loss (computed in the forward's epilogue);
+# with the one-launch raster kernel (every tile shape but 8x4) the stage
+# "raster" is the forward, the L1 term and the backward together
 STAGES = ["project", "bin_sort", "raster_fwd", "raster_bwd", "project_bwd"]
+STAGES_FUSED = ["project", "bin_sort", "raster", "project_bwd"]
 
 
 def parse():
@@ -55,6 +58,9 @@ def parse():
     ap.add_argument("--cpu-pixels", type=int, default=16384)
     ap.add_argument("--workload", type=int, default=3, choices=[3, 4, 5],
                     help="scene recipe: 3 = 1M Betas (default), 4 = 3M Betas, 5 = 6M Betas")
+    ap.add_argument("--raster", choices=["fused", "split"], default="fused",
+                    help="raster forward + L1 + backward in one launch per tile (fused), or as two launches "
+                         "(split); 8x4 tiles always split")
     ap.add_argument("--hit-masks", choices=["on", "off"], default="on",
                     help="the forward keeps its cover pass for the backward (on), or the backward recomputes "
                          "it (off)")
@@ -183,12 +189,18 @@ def hbm_roofline(stage_ms, ms_step, n, param_bytes, n_rec, K, px, peak, peak_src
       raster_bwd   record + index per pair, dL/dC, T,    K 52 + px 20 + n_rec 48
                    n_contrib read, 2D-gradient slots accumulated
       project_bwd  2D-gradient slots read and cleared,   n_rec 96 + 2 n P
-                   params read, gradients written"""
+                   params read, gradients written
+      raster       (the one-launch forward + L1 + backward) charged the sum
+                   of raster_fwd and raster_bwd above: the method's streams,
+                   although T, n_contrib and dL/dC stay in registers there"""
     b = {"project": n * param_bytes + n_rec * PROJ_BYTES,
          "bin_sort": n_rec * 28 + K * 20,
          "raster_fwd": K * (REC_BYTES + 4) + px * (20 + 12 + 12),
          "raster_bwd": K * (REC_BYTES + 4) + px * 20 + n_rec * GRAD2D_BYTES,
          "project_bwd": n_rec * 2 * GRAD2D_BYTES + 2 * n * param_bytes}
+    if "raster" in stage_ms:
+        b = {"project": b["project"], "bin_sort": b["bin_sort"], "raster": b["raster_fwd"] + b["raster_bwd"],
+             "project_bwd": b["project_bwd"]}
     out = {"peak_gbs": peak, "peak_kind": f"{peak_src} copy bandwidth", "stages": {}}
     for k, v in b.items():
         ms = stage_ms.get(k, 0.0)
@@ -313,6 +325,7 @@ def main():
         best, tune_ms = (tw_, th_, int(bsz), mode.upper() == "P"), {}
     else:
         best, tune_ms = autotune.tune(planes, sc.n, sc.n_lobes, cams, target, reps=3, hit_masks=hit_masks,
+                                      fused=args.raster == "fused",
                                       log=(lambda m: print(m, file=sys.stderr)) if rank == 0 else None)
     t_tune = time.perf_counter() - t_tune
     tw, th, bs, persist = best
@@ -320,7 +333,7 @@ def main():
     # on several GPUs the projection backward runs after the replay in chunks,
     # each chunk's gradient all-reduce overlapping the next chunks
     bstep = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, target, opts=opts, persistent=persist,
-                                hit_masks=hit_masks, graph_project_bwd=world == 1)
+                                hit_masks=hit_masks, graph_project_bwd=world == 1, fused=args.raster == "fused")
     rast = bstep.rast
     grad = bstep.grad
 
@@ -362,8 +375,10 @@ def main():
     value = pix_per_step / (ms_step * 1e-3) / 1e6
 
     # ---- per-stage times (separate loop, events between the entry points) ---
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(STAGES) + 1)]
-    stage_ms = {s: 0.0 for s in STAGES}
+    fused = bstep.fused
+    stages = STAGES_FUSED if fused else STAGES
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(stages) + 1)]
+    stage_ms = {s: 0.0 for s in stages}
     for _ in range(args.steps):
         ev[0].record(stream)
         rast.project(planes); ev[1].record(stream)
@@ -371,11 +386,14 @@ def main():
         if rast.persistent:
             rast.schedule()
         ev[2].record(stream)
-        rast.raster_fwd_l1(planes, target); ev[3].record(stream)
-        rast.raster_bwd(planes, rast.dL_dcolor); ev[4].record(stream)
-        rast.project_bwd(planes, grad); ev[5].record(stream)
+        if fused:
+            rast.raster_fwd_bwd_l1(planes, target); ev[3].record(stream)
+        else:
+            rast.raster_fwd_l1(planes, target); ev[3].record(stream)
+            rast.raster_bwd(planes, rast.dL_dcolor); ev[4].record(stream)
+        rast.project_bwd(planes, grad); ev[len(stages)].record(stream)
         torch.cuda.synchronize()
-        for k, s in enumerate(STAGES):
+        for k, s in enumerate(stages):
             stage_ms[s] += ev[k].elapsed_time(ev[k + 1]) / args.steps
 
     # ---- roofline of the dominant kernel -----------------------------------
@@ -392,10 +410,11 @@ def main():
     n_planes = scenes.n_planes(sc.n_lobes)
     hbm = hbm_roofline(stage_ms, ms_step, sc.n, n_planes * 4, V * sc.n, K, rast.total_pixels, hbm_peak,
                        peak_src)
-    if dom in ("raster_fwd", "raster_bwd"):
-        fl = FWD_FLOPS_PER_EVAL if dom == "raster_fwd" else BWD_FLOPS_PER_EVAL
+    if dom in ("raster_fwd", "raster_bwd", "raster"):
+        fl = {"raster_fwd": FWD_FLOPS_PER_EVAL, "raster_bwd": BWD_FLOPS_PER_EVAL,
+              "raster": FWD_FLOPS_PER_EVAL + BWD_FLOPS_PER_EVAL}[dom]
         achieved = evals * fl / (stage_ms[dom] * 1e-3) / 1e12
-        kname = "k_raster_fwd" if dom == "raster_fwd" else "k_raster_bwd"
+        kname = {"raster_fwd": "k_raster_fwd", "raster_bwd": "k_raster_bwd", "raster": "k_raster_step"}[dom]
         roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak, "traffic": ncu_traffic(kname, rast.total_pixels),
                 "peak_source": f"{n_sms} SMs x 128 FP32 lanes x 2 flop x max SM clock",
@@ -411,7 +430,8 @@ def main():
                 "frac": achieved / hbm_peak, "traffic": None}
     roof["peak_kind"] = f"{peak_src} (max SM clock {sm_max_mhz:.0f} MHz)" if roof["bound"] == "alu" else peak_src
     roof["hbm"] = hbm
-    roof["issue_active"] = {k: ncu_metric(k, "issue_active_pct") for k in ("k_raster_fwd", "k_raster_bwd")}
+    roof["issue_active"] = {k: ncu_metric(k, "issue_active_pct")
+                            for k in (("k_raster_step",) if fused else ("k_raster_fwd", "k_raster_bwd"))}
 
     extras = {}
     if not args.no_extras:
@@ -460,7 +480,7 @@ def main():
         h_loss = torch.empty(V, dtype=torch.float32).pin_memory()
         twin = batched.BatchedStep(torch.empty_like(planes).copy_(planes), sc.n, sc.n_lobes, cams,
                                    torch.empty_like(target).copy_(target), opts=opts, persistent=persist,
-                                   hit_masks=hit_masks, graph_project_bwd=world == 1)
+                                   hit_masks=hit_masks, graph_project_bwd=world == 1, fused=bstep.fused)
         twin.capture()
         steps2 = [bstep, twin]
         cin, cout = torch.cuda.Stream(), torch.cuda.Stream()
@@ -617,17 +637,20 @@ def main():
     # kernel launches of ours inside the timed region (all inside the replayed graph on
     # one GPU): project 3 (worklist reset, projection, rule-B2 tiles); bin_sort 5 (prep,
     # tile counts, scan, scatter, list sort); schedule 3 (persistent); raster fwd with
-    # the L1 term 2; raster bwd 1; project bwd 1 (one per chunk on several GPUs)
+    # the L1 term 2 and raster bwd 1, or the one-launch raster kernel and the L1
+    # reduce 2; project bwd 1 (one per chunk on several GPUs)
     from paper_2501_18630_gb300.distributed import chunk_ranges
     n_pbwd = len(chunk_ranges(sc.n, max(4, (sc.n + 7) // 8))) if world > 1 else 1
-    per_step = 3 + 5 + (3 if rast.persistent else 0) + 2 + 1 + n_pbwd
+    per_step = 3 + 5 + (3 if rast.persistent else 0) + (2 if fused else 3) + n_pbwd
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{sc.n} Betas (256 planar sheets, 3 SB lobes), {V} views {scenes.describe_sizes(cams)} "
                                f"per GPU, fwd+bwd with per-view L1 loss, one CUDA-graph replay per step",
-                   "tile": f"{tw}x{th}", "batch_s": bs, "persistent": persist, "hit_masks": hit_masks,
+                   "tile": f"{tw}x{th}", "batch_s": bs, "persistent": persist,
+                   "raster": "one launch (forward + L1 + backward)" if fused else "forward + L1, backward",
+                   "hit_masks": hit_masks and not fused,
                    "autotune": {"s": round(t_tune, 1), "ms": {f"{c[0]}x{c[1]}/S{c[2]}/{'P' if c[3] else 'G'}": round(v, 3)
                                                               for c, v in tune_ms.items()}},
                    "n_betas": sc.n, "views_per_gpu": V, "resolution": scenes.describe_sizes(cams),

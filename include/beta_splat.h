@@ -295,6 +295,35 @@ int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
                     const float* T_final, const uint32_t* n_contrib, const float* dL_dcolor, float* grad2d,
                     const int32_t* d_status, beta_stream_t stream);
 
+/* Steps 3 and 4a with the L1 loss between them, in one launch (Eq. C, the
+ * L1 term of Sec. 3.4 and the reverse-mode derivative of Eq. C): for every
+ * tile, one CTA composites the tile's pixels, forms their L1 term and
+ * dL/dC = sign(C - target) / (3 W_v H_v) in registers, and then walks the
+ * tile's list in reverse from those registers, adding the ten per-record sums
+ * of beta_raster_bwd into grad2d.  No per-pixel state passes through memory
+ * between the forward and the backward, and the backward finds the records
+ * the forward of the same tile just read in L2.
+ * The results are those of beta_raster_fwd_l1 followed by beta_raster_bwd on
+ * the same lists: color, T_final, n_contrib, dL_dcolor bit for bit, loss to
+ * the same fp32 summation order, and every term added to grad2d the same,
+ * with the sums differing only in the order of the floating-point atomic
+ * additions.
+ *   T_final, n_contrib, dL_dcolor  optional outputs (NULL: not written)
+ *   target, loss, ws, ws_bytes     as beta_raster_fwd_l1
+ *   grad2d    as beta_raster_bwd (zeros on entry, accumulated)
+ *   sched     beta_schedule() output for a persistent launch, or NULL
+ * Only tile shapes whose raster kernels give each thread a pair of pixels
+ * (every supported shape but 8 x 4) have this kernel: BETA_ERR_ARG for 8 x 4
+ * tiles (run beta_raster_fwd_l1 and beta_raster_bwd there), for null
+ * required pointers and a grad2d that is not 16-byte aligned;
+ * BETA_ERR_WORKSPACE for a short or misaligned ws. */
+int beta_raster_fwd_bwd_l1(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                           const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
+                           const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
+                           uint32_t* n_contrib, const float* target, float* loss, float* dL_dcolor,
+                           float* grad2d, void* ws, size_t ws_bytes, const int32_t* d_status,
+                           beta_stream_t stream);
+
 /* Step 4b (backward of Sec. 3.2 / Sec. 3.3): chains the 2D gradients of every
  * view through Sigma' = M M^T, M = J W R(q) S, mu'(t), t = W mu + t_w, the
  * sigmoid, beta = 4 e^b and the spherical-Beta colour to the raw parameters,

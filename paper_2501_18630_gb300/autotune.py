@@ -52,10 +52,11 @@ def _save(d):
     os.replace(tmp, p)
 
 
-def time_candidate(planes, n, n_lobes, cameras, target, cand, reps=5, hit_masks=True):
+def time_candidate(planes, n, n_lobes, cameras, target, cand, reps=5, hit_masks=True, fused=True):
     tw, th, s, persist = cand
     opts = _lib.default_opts(tile_w=tw, tile_h=th, batch_s=s)
-    step = BatchedStep(planes, n, n_lobes, cameras, target, opts=opts, persistent=persist, hit_masks=hit_masks)
+    step = BatchedStep(planes, n, n_lobes, cameras, target, opts=opts, persistent=persist, hit_masks=hit_masks,
+                       fused=fused)
     step.step()
     step.check()
     stream = torch.cuda.current_stream()
@@ -72,10 +73,11 @@ def time_candidate(planes, n, n_lobes, cameras, target, cand, reps=5, hit_masks=
 
 
 def tune(planes, n, n_lobes, cameras, target, candidates=None, reps=5, use_cache=True, log=None,
-         hit_masks=True):
+         hit_masks=True, fused=True):
     """Returns (best candidate, {candidate: ms}).  Candidates are tuples
-    (tile_w, tile_h, batch_s, persistent)."""
-    key = workload_key(n, n_lobes, cameras, planes.device) + f";hm={int(hit_masks)}"
+    (tile_w, tile_h, batch_s, persistent); fused selects the one-launch raster
+    forward + backward where the tile shape has it (BatchedStep's fused)."""
+    key = workload_key(n, n_lobes, cameras, planes.device) + f";hm={int(hit_masks)};fused={int(fused)}"
     cache = _load() if use_cache else {}
     if use_cache and key in cache:
         e = cache[key]
@@ -83,7 +85,7 @@ def tune(planes, n, n_lobes, cameras, target, candidates=None, reps=5, use_cache
     times = {}
     for cand in (candidates or CANDIDATES):
         t0 = time.perf_counter()
-        times[tuple(cand)] = time_candidate(planes, n, n_lobes, cameras, target, cand, reps, hit_masks)
+        times[tuple(cand)] = time_candidate(planes, n, n_lobes, cameras, target, cand, reps, hit_masks, fused)
         if log:
             log(f"autotune {cand}: {times[tuple(cand)]:.3f} ms ({time.perf_counter() - t0:.1f} s)")
     best = min(times, key=times.get)

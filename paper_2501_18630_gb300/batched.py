@@ -1,8 +1,9 @@
 """Batched forward + backward of many views as one replayable CUDA graph.
 
-The whole step -- project, bin/sort, longest-first schedule, persistent
-raster forward with the per-view L1 loss in its epilogue, persistent raster
-backward, projection backward -- is captured once and replayed.  Every entry point only enqueues
+The whole step -- project, bin/sort, longest-first schedule, raster forward
+with the per-view L1 loss in its epilogue, raster backward (for the tile
+shapes with pixel-pair kernels both in one launch, beta_raster_fwd_bwd_l1),
+projection backward -- is captured once and replayed.  Every entry point only enqueues
 kernels and the pair count stays on the device, so nothing in the step
 synchronises with the host.  A pair-capacity overflow shows up in the device
 status word; check() reads it (one sync), grows the buffers and recaptures.
@@ -20,15 +21,19 @@ from .render import Rasterizer
 class BatchedStep:
     def __init__(self, planes: torch.Tensor, n: int, n_lobes: int, cameras, target: torch.Tensor,
                  opts: _lib.BetaOpts | None = None, persistent: bool = True, headroom: float = 1.15,
-                 hit_masks: bool = True, graph_project_bwd: bool = True):
+                 hit_masks: bool = True, graph_project_bwd: bool = True, fused: bool = True):
         """graph_project_bwd=False leaves the projection backward out of the
         captured graph, for project_bwd_reduced() to run it in chunks, each
-        chunk's gradient all-reduce overlapping the next chunk."""
+        chunk's gradient all-reduce overlapping the next chunk.  fused=False
+        runs the raster forward (+ L1) and backward as two launches even where
+        the one-launch kernel exists; hit masks only serve that split path."""
         self.planes = planes
         self.target = target
         self.graph_project_bwd = bool(graph_project_bwd)
         self.rast = Rasterizer(n, planes.shape[1], n_lobes, cameras, opts, device=planes.device,
-                               persistent=persistent, hit_masks=hit_masks)
+                               persistent=persistent)
+        self.fused = bool(fused) and self.rast.fused_supported
+        self.rast.use_hit_masks = bool(hit_masks) and not self.fused   # allocated by _size_pairs
         self.grad = torch.zeros_like(planes)
         self.headroom = headroom
         self.graph = None
@@ -47,8 +52,11 @@ class BatchedStep:
         r.bin_sort(self.planes)
         if r.persistent:
             r.schedule()
-        r.raster_fwd_l1(self.planes, self.target)
-        r.raster_bwd(self.planes, r.dL_dcolor)
+        if self.fused:
+            r.raster_fwd_bwd_l1(self.planes, self.target)
+        else:
+            r.raster_fwd_l1(self.planes, self.target)
+            r.raster_bwd(self.planes, r.dL_dcolor)
         if self.graph_project_bwd:
             r.project_bwd(self.planes, self.grad)
 

@@ -369,6 +369,28 @@ int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
                                        (uint32_t*)sched, hm, (cudaStream_t)stream));
 }
 
+int beta_raster_fwd_bwd_l1(const beta_params* prm, const beta_camera* cams, int32_t n_views,
+                           const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
+                           const uint32_t* tile_ranges, void* sched, float* color, float* T_final,
+                           uint32_t* n_contrib, const float* target, float* loss, float* dL_dcolor,
+                           float* grad2d, void* ws, size_t ws_bytes, const int32_t* d_status,
+                           beta_stream_t stream) {
+  if (!valid_params(prm) || !proj || !aligned16(proj) || !tile_ranges || !color || !target || !loss ||
+      !grad2d || !aligned16(grad2d) || !d_status)
+    return BETA_ERR_ARG;
+  int e = check_opts(opt);
+  if (e != BETA_OK) return e;
+  if (!raster_step_supported(render_opts(opt))) return BETA_ERR_ARG;
+  ViewTable vt;
+  if ((e = build_views(cams, n_views, opt, vt)) != BETA_OK) return e;
+  if (sched && ((uintptr_t)sched & 3u)) return BETA_ERR_ARG;
+  if (!ws || ws_bytes < fwd_l1_ws_bytes(vt) || ((uintptr_t)ws & 3u)) return BETA_ERR_WORKSPACE;
+  ProjBuffers pb = proj_layout((void*)proj, prm->pitch, n_views);
+  return cuda_status(launch_raster_step_l1(vt, render_opts(opt), pb.rec, pair_vals, tile_ranges, color, T_final,
+                                           n_contrib, d_status, (uint32_t*)sched, target, loss, dL_dcolor,
+                                           (float*)ws, grad2d, (cudaStream_t)stream));
+}
+
 int beta_project_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                      const beta_opts* opt, float* grad2d, float* grad_planes,
                      const int32_t* d_status, beta_stream_t stream) {

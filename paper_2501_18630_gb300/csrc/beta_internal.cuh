@@ -529,6 +529,12 @@ cudaError_t launch_raster_fwd_l1(const ViewTable& vt, const RenderOpts& ro, cons
                                  float* T_final, uint32_t* n_contrib, const int32_t* status,
                                  uint32_t* sched, const float* target, float* loss, float* dL_dcolor,
                                  float* ws, HitMasks hm, cudaStream_t s);
+// forward + L1 + backward in one launch (tile shapes with pixel pairs)
+bool raster_step_supported(const RenderOpts& ro);
+cudaError_t launch_raster_step_l1(const ViewTable& vt, const RenderOpts& ro, const float4* rec,
+                                  const uint32_t* vals, const uint32_t* ranges, float* color, float* T_final,
+                                  uint32_t* n_contrib, const int32_t* status, uint32_t* sched, const float* target,
+                                  float* loss, float* dL_dcolor, float* ws, float* grad2d, cudaStream_t s);
 size_t l1_ws_bytes(const ViewTable& vt);
 cudaError_t launch_l1(const ViewTable& vt, const float* color, const float* target, float* loss,
                       float* dL_dcolor, float* ws, cudaStream_t s);

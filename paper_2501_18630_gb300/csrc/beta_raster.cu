@@ -728,6 +728,195 @@ __device__ __forceinline__ void rec_r2_pair(float4 f0, float4 f1, float xf, floa
   r2b = fmaf(u1, u1, v1 * v1);
 }
 
+// Per-lane state of the pixel-pair forward after a tile's walk: transmittance,
+// accumulated colour and last contributor (1-based list position, 0 for none)
+// of the lane's two pixels.
+struct PairFwdState {
+  float T0, T1, C00, C01, C02, C10, C11, C12;
+  uint32_t last0, last1;
+};
+
+// Forward walk of one tile's list [start, end) at the lane's pixel pair (xf,
+// yf), (xf + 1, yf) of the warp block whose first pixel is (bxf, byf): records
+// staged S per batch (double-buffered cp.async, the list entries of the next
+// batch loaded one batch ahead); per 32-record chunk the warp's cover pass and
+// bit transpose, then every lane composites its records in list order at both
+// pixels (Eq. C), until T < t_eps at every pixel of the CTA.  With hslot the
+// chunks' cover masks are stored for the backward.  Returns with every copy
+// landed; the caller synchronises the CTA before s_rec is staged again.
+template <int TW, int TH, int S>
+__device__ __forceinline__ void pair_fwd_walk(float4 (&s_rec)[2][S][kRecordF4], const float4* __restrict__ rec,
+                                              const uint32_t* __restrict__ vals, uint32_t start, uint32_t end,
+                                              uint32_t* hslot, float xf, float yf, float bxf, float byf, bool in0,
+                                              bool in1, float t_eps, float amax, PairFwdState& st) {
+  using PB = PairBlock<TW>;
+  constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  // batch 0 goes to buffer 0 now; the list entries of batch 1 are loaded
+  // ahead so that its copies can be issued without waiting on them
+  uint32_t rn[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) {
+    const int jj = tid + q * NT;
+    if (jj < S && start + jj < end) stage_record(s_rec[0][jj], rec, vals[start + jj]);
+    const uint32_t j1 = start + S + jj;
+    rn[q] = (jj < S && j1 < end) ? vals[j1] : 0u;
+  }
+  cp_async_commit();
+
+  float T0 = 1.0f, T1 = 1.0f, C00 = 0.0f, C01 = 0.0f, C02 = 0.0f, C10 = 0.0f, C11 = 0.0f, C12 = 0.0f;
+  uint32_t last0 = 0, last1 = 0;
+  bool done0 = !in0, done1 = !in1;
+  bool warp_done = __all_sync(0xffffffffu, done0 && done1);
+
+  int buf = 0;
+  for (uint32_t base = start; base < end; base += S) {
+    cp_async_wait_all();
+    if (!__syncthreads_or(!(done0 && done1))) break;
+    const uint32_t nb = base + S;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int jj = tid + q * NT;
+      if (jj < S && nb + jj < end) stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
+      const uint32_t j2 = nb + S + jj;
+      rn[q] = (jj < S && j2 < end) ? vals[j2] : 0u;
+    }
+    cp_async_commit();
+    const int cnt = (int)min((uint32_t)S, end - base);
+    for (int c = 0; c < cnt && !warp_done; c += 32) {
+      // pass 1: lane k finds the pairs of this warp's block that record
+      // c + k may cover; the transpose gives every lane its records
+      const int idx = c + lane;
+      const uint32_t cov =
+          idx < cnt ? pair_cover<PB::BW>(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
+      uint32_t mine = transpose32(cov, lane);
+      if (hslot) {
+        uint32_t* slot = hslot + (size_t)((base - start + c) >> 5) * (NT + NW);
+        const uint32_t wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
+        slot[tid] = mine;
+        if (lane == 0) slot[NT + warp] = wide;
+      }
+      if (done0 && done1) mine = 0u;
+      // pass 2: every lane composites its records in list order at both
+      // of its pixels
+      while (mine) {
+        const int k = __ffs(mine) - 1;
+        mine &= mine - 1;
+        const int s = c + k;
+        const float4 f0 = s_rec[buf][s][0];
+        const float4 f1 = s_rec[buf][s][1];
+        float u0, v0, u1, v1, r2a, r2b;
+        rec_r2_pair(f0, f1, xf, yf, u0, v0, u1, v1, r2a, r2b);
+        const bool h0 = !done0 && r2a < 1.0f, h1 = !done1 && r2b < 1.0f;
+        if (!(h0 || h1)) continue;                    // outside the support (the cover is conservative)
+        const float4 f2 = s_rec[buf][s][2];
+        const uint32_t pos = base - start + (uint32_t)s + 1u;
+        if (h0) {
+          const float a = fminf(ex2_approx(fmaf(f1.w, lg2_approx(1.0f - r2a), f2.x)), amax);
+          const float w = a * T0;
+          C00 = fmaf(w, f2.y, C00);
+          C01 = fmaf(w, f2.z, C01);
+          C02 = fmaf(w, f2.w, C02);
+          T0 = T0 * (1.0f - a);
+          last0 = pos;
+          done0 = T0 < t_eps;
+        }
+        if (h1) {
+          const float a = fminf(ex2_approx(fmaf(f1.w, lg2_approx(1.0f - r2b), f2.x)), amax);
+          const float w = a * T1;
+          C10 = fmaf(w, f2.y, C10);
+          C11 = fmaf(w, f2.z, C11);
+          C12 = fmaf(w, f2.w, C12);
+          T1 = T1 * (1.0f - a);
+          last1 = pos;
+          done1 = T1 < t_eps;
+        }
+        if (done0 && done1) mine = 0u;
+      }
+      warp_done = __all_sync(0xffffffffu, done0 && done1);
+    }
+    buf ^= 1;
+  }
+  cp_async_wait_all();   // no copy may still land in a buffer the next tile fills
+  st.T0 = T0;
+  st.T1 = T1;
+  st.C00 = C00;
+  st.C01 = C01;
+  st.C02 = C02;
+  st.C10 = C10;
+  st.C11 = C11;
+  st.C12 = C12;
+  st.last0 = last0;
+  st.last1 = last1;
+}
+
+// Epilogue of the pixel-pair forward at pixels (x, y), (x + 1, y) of view v:
+// the colour C + T bg to color; T and the last contributor to Tout / ncontrib
+// when those are given; with a target (tgt[ch][2 tid + i]: pixel i, channel
+// ch, landed in shared memory) the L1 term, whose gradient
+// sign(C - target) / (3 H W) goes to dLdC when given and to gv (pixel i,
+// channel ch at gv[3 i + ch]; zero off the image or without a target).
+// Returns the lane's sum of |C - target|.
+template <int NT>
+__device__ __forceinline__ float pair_fwd_out(const PairFwdState& st, const ViewTable& vt, int v, int x, int y,
+                                              bool in0, bool in1, bool with_target, const float (&tgt)[3][2 * NT],
+                                              float* __restrict__ color, float* __restrict__ Tout,
+                                              uint32_t* __restrict__ ncontrib, float* __restrict__ dLdC,
+                                              float (&gv)[6]) {
+  const int tid = threadIdx.x;
+  const int W = vt.v[v].width, H = vt.v[v].height;
+  const int64_t HW = (int64_t)W * H;
+  const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
+  const int64_t o = 3 * vt.v[v].pix_off + (int64_t)y * W + x;
+  const float scale = 1.0f / (3.0f * (float)HW);
+  float l1 = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) gv[3 * i + ch] = 0.0f;
+    if (!(i == 0 ? in0 : in1)) continue;
+    const float T = i == 0 ? st.T0 : st.T1;
+    const float c[3] = {(i == 0 ? st.C00 : st.C10) + T * vt.v[v].bg[0], (i == 0 ? st.C01 : st.C11) + T * vt.v[v].bg[1],
+                        (i == 0 ? st.C02 : st.C12) + T * vt.v[v].bg[2]};
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) color[o + i + ch * HW] = c[ch];
+    if (Tout) Tout[pix + i] = T;
+    if (ncontrib) ncontrib[pix + i] = i == 0 ? st.last0 : st.last1;
+    if (with_target) {
+      // the per-pixel L1 term and its gradient, as beta_l1_loss computes them
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float d = c[ch] - tgt[ch][2 * tid + i];
+        l1 += fabsf(d);
+        const float gd = d > 0.0f ? scale : (d < 0.0f ? -scale : 0.0f);
+        gv[3 * i + ch] = gd;
+        if (dLdC) dLdC[o + i + ch * HW] = gd;
+      }
+    }
+  }
+  return l1;
+}
+
+// The CTA's sum of the lanes' l1 in a fixed order (warp shuffles, then the
+// warps in index order), stored to *out.  Synchronises the CTA on entry and
+// exit.
+template <int NW>
+__device__ __forceinline__ void tile_l1_partial(float l1, float (&s_l1)[NW], float* out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+  if (lane == 0) s_l1[warp] = l1;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.0f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) t += s_l1[w];
+    *out = t;
+  }
+  __syncthreads();
+}
+
 template <int TW, int TH, int S, bool PERSIST>
 __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_threads_per_sm(S))) k_raster_fwd2(
     ViewTable vt, RenderOpts ro, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
@@ -736,7 +925,7 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
     const uint32_t* __restrict__ order, const float* __restrict__ target, float* __restrict__ dLdC,
     float* __restrict__ l1_partial, uint32_t* __restrict__ hm, size_t hm_words) {
   using PB = PairBlock<TW>;
-  constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
+  constexpr int NT = TW * TH / 2, NW = NT / 32;
   static_assert(pair_tiles(TW, TH) && TH % PB::BH == 0 && NT % 32 == 0, "tile must hold whole pair blocks");
   __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
   __shared__ float s_l1[NW];
@@ -755,7 +944,6 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
     const int bx = tx * TW + (warp % PB::WX) * PB::BW, by = ty * TH + (warp / PB::WX) * PB::BH;
     const int x = bx + 2 * (lane % PB::PC), y = by + lane / PB::PC;   // pixels (x, y), (x + 1, y)
     const bool in0 = x < W && y < H, in1 = x + 1 < W && y < H;
-    const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
     const uint32_t start = ranges[g], end = ranges[g + 1];
     uint32_t* const hslot = hit_tile<NT>(hm, hm_words, start, end, g);
     if (target) {
@@ -767,134 +955,14 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
         if (in1) cp_async4(&s_tgt[ch][2 * tid + 1], target + o + 1 + ch * HW);
       }
     }
-
-    // batch 0 goes to buffer 0 now; the list entries of batch 1 are loaded
-    // ahead so that its copies can be issued without waiting on them
-    uint32_t rn[RPT];
-#pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-      const int jj = tid + q * NT;
-      if (jj < S && start + jj < end) stage_record(s_rec[0][jj], rec, vals[start + jj]);
-      const uint32_t j1 = start + S + jj;
-      rn[q] = (jj < S && j1 < end) ? vals[j1] : 0u;
-    }
-    cp_async_commit();
-
-    float T0 = 1.0f, T1 = 1.0f, C00 = 0.0f, C01 = 0.0f, C02 = 0.0f, C10 = 0.0f, C11 = 0.0f, C12 = 0.0f;
-    uint32_t last0 = 0, last1 = 0;
-    bool done0 = !in0, done1 = !in1;
-    bool warp_done = __all_sync(0xffffffffu, done0 && done1);
-
-    int buf = 0;
-    for (uint32_t base = start; base < end; base += S) {
-      cp_async_wait_all();
-      if (!__syncthreads_or(!(done0 && done1))) break;
-      const uint32_t nb = base + S;
-#pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int jj = tid + q * NT;
-        if (jj < S && nb + jj < end) stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
-        const uint32_t j2 = nb + S + jj;
-        rn[q] = (jj < S && j2 < end) ? vals[j2] : 0u;
-      }
-      cp_async_commit();
-      const int cnt = (int)min((uint32_t)S, end - base);
-      for (int c = 0; c < cnt && !warp_done; c += 32) {
-        // pass 1: lane k finds the pairs of this warp's block that record
-        // c + k may cover; the transpose gives every lane its records
-        const int idx = c + lane;
-        const uint32_t cov =
-            idx < cnt ? pair_cover<PB::BW>(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
-        uint32_t mine = transpose32(cov, lane);
-        if (hslot) {
-          uint32_t* slot = hslot + (size_t)((base - start + c) >> 5) * (NT + NW);
-          const uint32_t wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
-          slot[tid] = mine;
-          if (lane == 0) slot[NT + warp] = wide;
-        }
-        if (done0 && done1) mine = 0u;
-        // pass 2: every lane composites its records in list order at both
-        // of its pixels
-        while (mine) {
-          const int k = __ffs(mine) - 1;
-          mine &= mine - 1;
-          const int s = c + k;
-          const float4 f0 = s_rec[buf][s][0];
-          const float4 f1 = s_rec[buf][s][1];
-          float u0, v0, u1, v1, r2a, r2b;
-          rec_r2_pair(f0, f1, xf, yf, u0, v0, u1, v1, r2a, r2b);
-          const bool h0 = !done0 && r2a < 1.0f, h1 = !done1 && r2b < 1.0f;
-          if (!(h0 || h1)) continue;                    // outside the support (the cover is conservative)
-          const float4 f2 = s_rec[buf][s][2];
-          const uint32_t pos = base - start + (uint32_t)s + 1u;
-          if (h0) {
-            const float a = fminf(ex2_approx(fmaf(f1.w, lg2_approx(1.0f - r2a), f2.x)), amax);
-            const float w = a * T0;
-            C00 = fmaf(w, f2.y, C00);
-            C01 = fmaf(w, f2.z, C01);
-            C02 = fmaf(w, f2.w, C02);
-            T0 = T0 * (1.0f - a);
-            last0 = pos;
-            done0 = T0 < t_eps;
-          }
-          if (h1) {
-            const float a = fminf(ex2_approx(fmaf(f1.w, lg2_approx(1.0f - r2b), f2.x)), amax);
-            const float w = a * T1;
-            C10 = fmaf(w, f2.y, C10);
-            C11 = fmaf(w, f2.z, C11);
-            C12 = fmaf(w, f2.w, C12);
-            T1 = T1 * (1.0f - a);
-            last1 = pos;
-            done1 = T1 < t_eps;
-          }
-          if (done0 && done1) mine = 0u;
-        }
-        warp_done = __all_sync(0xffffffffu, done0 && done1);
-      }
-      buf ^= 1;
-    }
-    cp_async_wait_all();   // no copy may still land in a buffer the next tile fills
-    float l1 = 0.0f;
-    {
-      const int64_t HW = (int64_t)W * H;
-      const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
-      const int64_t o = 3 * vt.v[v].pix_off + (int64_t)y * W + x;
-      const float scale = 1.0f / (3.0f * (float)HW);
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        if (!(i == 0 ? in0 : in1)) continue;
-        const float T = i == 0 ? T0 : T1;
-        const float c[3] = {(i == 0 ? C00 : C10) + T * vt.v[v].bg[0], (i == 0 ? C01 : C11) + T * vt.v[v].bg[1],
-                            (i == 0 ? C02 : C12) + T * vt.v[v].bg[2]};
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) color[o + i + ch * HW] = c[ch];
-        Tout[pix + i] = T;
-        ncontrib[pix + i] = i == 0 ? last0 : last1;
-        if (target) {
-          // the per-pixel L1 term and its gradient, as beta_l1_loss computes them
-#pragma unroll
-          for (int ch = 0; ch < 3; ++ch) {
-            const float d = c[ch] - s_tgt[ch][2 * tid + i];   // landed: the copies were waited for above
-            l1 += fabsf(d);
-            dLdC[o + i + ch * HW] = d > 0.0f ? scale : (d < 0.0f ? -scale : 0.0f);
-          }
-        }
-      }
-    }
-    if (target) {
-      // tile partial sum of |C - target|, reduced in a fixed order
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
-      if (lane == 0) s_l1[warp] = l1;
-      __syncthreads();
-      if (tid == 0) {
-        float t = 0.0f;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) t += s_l1[w];
-        l1_partial[g] = t;
-      }
-      __syncthreads();
-    }
+    PairFwdState fs;
+    pair_fwd_walk<TW, TH, S>(s_rec, rec, vals, start, end, hslot, (float)x, (float)y, (float)bx, (float)by, in0,
+                             in1, t_eps, amax, fs);
+    float gv[6];
+    const float l1 = pair_fwd_out<NT>(fs, vt, v, x, y, in0, in1, target != nullptr, s_tgt, color, Tout, ncontrib,
+                                      dLdC, gv);
+    // tile partial sum of |C - target|, reduced in a fixed order
+    if (target) tile_l1_partial<NW>(l1, s_l1, l1_partial + g);
   }
   leave<PERSIST>(ctr);
 }
@@ -926,6 +994,166 @@ __device__ __forceinline__ bool pix_terms(float u, float vv, float r2, float4 f1
   return act;
 }
 
+// Per-lane state the pixel-pair backward starts from: final transmittance,
+// the suffix colour term g . S (the background's, T bg . g), dL/dC and the
+// last-contributor position of the lane's two pixels (zeros off the image).
+struct PairBwdState {
+  float T0, T1, GS0, GS1, g0x, g0y, g0z, g1x, g1y, g1z;
+  uint32_t nl0, nl1;
+};
+
+// Reverse walk of one tile's list lst at the lane's pixel pair, from the CTA's
+// largest last-contributor position down: batches of S records staged as the
+// forward staged them (so chunks start at multiples of 32), the list entries
+// of the next batch down loaded one batch ahead; per chunk the cover masks
+// (the forward's from hslot, else the cover pass again), then every lane's
+// walk of its records in reverse list order at both pixels with three vector
+// atomics per record, and records covering more than kLaneAtomics of the
+// warp's pairs by the whole warp (reduce-scatter, one atomic per value).
+// Returns with every copy landed and the CTA synchronised.
+template <int TW, int TH, int S>
+__device__ __forceinline__ void pair_bwd_walk(float4 (&s_rec)[2][S][kRecordF4], uint32_t (&s_ridx)[2][S],
+                                              uint32_t (&s_wmax)[TW * TH / 64], const float4* __restrict__ rec,
+                                              const uint32_t* __restrict__ lst, const uint32_t* hslot,
+                                              float* __restrict__ grad2d, float xf, float yf, float bxf, float byf,
+                                              float amax, int my_field, const PairBwdState& st) {
+  using PB = PairBlock<TW>;
+  constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float T0 = st.T0, T1 = st.T1, GS0 = st.GS0, GS1 = st.GS1;
+  const float g0x = st.g0x, g0y = st.g0y, g0z = st.g0z, g1x = st.g1x, g1y = st.g1y, g1z = st.g1z;
+  const uint32_t nl0 = st.nl0, nl1 = st.nl1;
+  const uint32_t nlm = max(nl0, nl1);
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, nlm);
+  if (lane == 0) s_wmax[warp] = wmax;
+  __syncthreads();
+  int bmax = 0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) bmax = max(bmax, (int)s_wmax[w]);
+
+  // Batch b covers list positions [b S, min(b S + S, bmax)), b = nb - 1 .. 0
+  // (the forward's batches, so chunks start at multiples of 32).  The last
+  // goes to buffer 0 now; the list entries of the one before it are loaded
+  // ahead so that its copies issue without waiting.
+  const int nb = (bmax + S - 1) / S;
+  uint32_t rn[RPT];
+  {
+    const int lo0 = (nb - 1) * S, lo1 = lo0 - S;
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int jj = tid + q * NT;
+      if (nb > 0 && jj < bmax - lo0) {
+        const uint32_t r = lst[lo0 + jj];
+        s_ridx[0][jj] = r;
+        stage_record(s_rec[0][jj], rec, r);
+      }
+      rn[q] = (lo1 >= 0 && jj < S) ? lst[lo1 + jj] : 0u;
+    }
+    cp_async_commit();
+  }
+
+  // hit masks of the next chunk (chunks are walked from the last down),
+  // loaded one chunk ahead so that their DRAM latency overlaps a chunk
+  uint32_t pf_mine = 0u, pf_wide = 0u;
+  int pf_chunk = -1;
+  int buf = 0;
+  for (int b = nb - 1; b >= 0; --b) {
+    const int lo = b * S;
+    const int cnt = min(S, bmax - lo);
+    cp_async_wait_all();
+    __syncthreads();
+    {
+      // copies of batch b - 1 (full) into the other buffer, entries of b - 2
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int jj = tid + q * NT;
+        if (b >= 1 && jj < S) {
+          s_ridx[buf ^ 1][jj] = rn[q];
+          stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
+        }
+        rn[q] = (b >= 2 && jj < S) ? lst[(b - 2) * S + jj] : 0u;
+      }
+      cp_async_commit();
+    }
+    for (int c = ((cnt - 1) >> 5) << 5; c >= 0; c -= 32) {
+      if ((uint32_t)(lo + c) >= wmax) continue;
+      uint32_t wide, mine;
+      if (hslot) {
+        const int j = (lo + c) >> 5;
+        if (pf_chunk == j) {                           // the forward's pass 1
+          mine = pf_mine;
+          wide = pf_wide;
+        } else {
+          const uint32_t* slot = hslot + (size_t)j * (NT + NW);
+          mine = slot[tid];
+          wide = slot[NT + warp];
+        }
+        if (j >= 1) {
+          const uint32_t* nslot = hslot + (size_t)(j - 1) * (NT + NW);
+          pf_mine = nslot[tid];
+          pf_wide = nslot[NT + warp];
+          pf_chunk = j - 1;
+        }
+        const int limw = (int)wmax - (lo + c);         // no lane of the warp reaches past wmax
+        wide &= limw >= 32 ? 0xffffffffu : (1u << limw) - 1u;
+      } else {
+        const int idx = c + lane;
+        const uint32_t cov = (idx < cnt && (uint32_t)(lo + idx) < wmax)
+                                 ? pair_cover<PB::BW>(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
+        wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
+        mine = transpose32(cov, lane);
+      }
+      const int lim = (int)nlm - (lo + c);           // only positions before a pixel's last contributor
+      mine &= lim >= 32 ? 0xffffffffu : (lim <= 0 ? 0u : (1u << lim) - 1u);
+      // pass 2, in reverse list order: between wide records every lane walks
+      // its own records at both of its pixels and adds their summed terms
+      // with three vector atomics; a wide record is done by the whole warp
+      // together (reduce-scatter, one atomic per value)
+      for (;;) {
+        const int kb = wide ? 31 - __clz(wide) : -1;                 // warp-uniform
+        const uint32_t above = kb >= 0 ? ~((2u << kb) - 1u) : 0xffffffffu;
+        uint32_t seg = mine & above;
+        mine &= ~above;
+        while (seg) {
+          const int k = 31 - __clz(seg);
+          seg &= ~(1u << k);
+          const int s = c + k;
+          const uint32_t pos = (uint32_t)(lo + s);
+          const float4 f0 = s_rec[buf][s][0], f1 = s_rec[buf][s][1], f2 = s_rec[buf][s][2];
+          float u0, v0, u1, v1, r2a, r2b;
+          rec_r2_pair(f0, f1, xf, yf, u0, v0, u1, v1, r2a, r2b);
+          float G[kGrad2d];
+          const bool a0 = pix_terms<false>(u0, v0, r2a, f1, f2, amax, pos < nl0, g0x, g0y, g0z, T0, GS0, G);
+          const bool a1 = pix_terms<true>(u1, v1, r2b, f1, f2, amax, pos < nl1, g1x, g1y, g1z, T1, GS1, G);
+          if (!(a0 || a1)) continue;                  // outside the support (the cover is conservative)
+          float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
+          red_add_v4(gdst + 0, G[0], G[1], G[2], G[3]);
+          red_add_v4(gdst + 4, G[4], G[5], G[6], G[7]);
+          red_add_v4(gdst + 8, G[8], G[9], 0.0f, 0.0f);
+        }
+        if (kb < 0) break;
+        wide &= ~(1u << kb);
+        const bool mine_kb = (mine >> kb) & 1u;
+        mine &= ~(1u << kb);
+        const int s = c + kb;
+        const uint32_t pos = (uint32_t)(lo + s);
+        const float4 f0 = s_rec[buf][s][0], f1 = s_rec[buf][s][1], f2 = s_rec[buf][s][2];
+        float u0, v0, u1, v1, r2a, r2b;
+        rec_r2_pair(f0, f1, xf, yf, u0, v0, u1, v1, r2a, r2b);
+        float G[kGrad2d];                              // zero where a pixel is not covered
+        pix_terms<false>(u0, v0, r2a, f1, f2, amax, mine_kb && pos < nl0, g0x, g0y, g0z, T0, GS0, G);
+        pix_terms<true>(u1, v1, r2b, f1, f2, amax, mine_kb && pos < nl1, g1x, g1y, g1z, T1, GS1, G);
+        const float tot = warp_sum10(G, lane);
+        float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
+        if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
+      }
+    }
+    buf ^= 1;
+  }
+  cp_async_wait_all();   // no copy may still land in a buffer the next tile fills
+  __syncthreads();
+}
+
 template <int TW, int TH, int S, bool PERSIST>
 __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_threads_per_sm(S))) k_raster_bwd2(
     ViewTable vt, RenderOpts ro, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
@@ -933,7 +1161,7 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
     const float* __restrict__ dLdC, float* __restrict__ grad2d, const int32_t* __restrict__ status, uint32_t* ctr,
     const uint32_t* __restrict__ order, const uint32_t* __restrict__ hm, size_t hm_words) {
   using PB = PairBlock<TW>;
-  constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
+  constexpr int NT = TW * TH / 2, NW = NT / 32;
   static_assert(pair_tiles(TW, TH) && TH % PB::BH == 0 && NT % 32 == 0, "tile must hold whole pair blocks");
   __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
   __shared__ uint32_t s_ridx[2][S];
@@ -953,165 +1181,120 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
     const int bx = tx * TW + (warp % PB::WX) * PB::BW, by = ty * TH + (warp / PB::WX) * PB::BH;
     const int x = bx + 2 * (lane % PB::PC), y = by + lane / PB::PC;   // pixels (x, y), (x + 1, y)
     const bool in0 = x < W && y < H, in1 = x + 1 < W && y < H;
-    const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
     const uint32_t range0 = ranges[g];
-    const uint32_t* lst = vals + range0;
     const uint32_t* const hslot = hit_tile<NT>(const_cast<uint32_t*>(hm), hm_words, range0, ranges[g + 1], g);
 
-    float T0 = 1.0f, T1 = 1.0f, GS0 = 0.0f, GS1 = 0.0f;
-    float g0x = 0.0f, g0y = 0.0f, g0z = 0.0f, g1x = 0.0f, g1y = 0.0f, g1z = 0.0f;
-    uint32_t nl0 = 0, nl1 = 0;
+    PairBwdState bs{1.0f, 1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0u, 0u};
     {
       const int64_t HW = (int64_t)W * H;
       const int64_t pix = vt.v[v].pix_off + (int64_t)y * W + x;
       const float* gb = dLdC + 3 * vt.v[v].pix_off + (int64_t)y * W + x;
       const float* bg = vt.v[v].bg;
       if (in0) {
-        g0x = gb[0];
-        g0y = gb[HW];
-        g0z = gb[2 * HW];
-        T0 = Tfin[pix];
-        nl0 = ncontrib[pix];
-        GS0 = T0 * (g0x * bg[0] + g0y * bg[1] + g0z * bg[2]);
+        bs.g0x = gb[0];
+        bs.g0y = gb[HW];
+        bs.g0z = gb[2 * HW];
+        bs.T0 = Tfin[pix];
+        bs.nl0 = ncontrib[pix];
+        bs.GS0 = bs.T0 * (bs.g0x * bg[0] + bs.g0y * bg[1] + bs.g0z * bg[2]);
       }
       if (in1) {
-        g1x = gb[1];
-        g1y = gb[HW + 1];
-        g1z = gb[2 * HW + 1];
-        T1 = Tfin[pix + 1];
-        nl1 = ncontrib[pix + 1];
-        GS1 = T1 * (g1x * bg[0] + g1y * bg[1] + g1z * bg[2]);
+        bs.g1x = gb[1];
+        bs.g1y = gb[HW + 1];
+        bs.g1z = gb[2 * HW + 1];
+        bs.T1 = Tfin[pix + 1];
+        bs.nl1 = ncontrib[pix + 1];
+        bs.GS1 = bs.T1 * (bs.g1x * bg[0] + bs.g1y * bg[1] + bs.g1z * bg[2]);
       }
     }
-    const uint32_t nlm = max(nl0, nl1);
-    const uint32_t wmax = __reduce_max_sync(0xffffffffu, nlm);
-    if (lane == 0) s_wmax[warp] = wmax;
-    __syncthreads();
-    int bmax = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) bmax = max(bmax, (int)s_wmax[w]);
+    pair_bwd_walk<TW, TH, S>(s_rec, s_ridx, s_wmax, rec, vals + range0, hslot, grad2d, (float)x, (float)y,
+                             (float)bx, (float)by, amax, my_field, bs);
+  }
+  leave<PERSIST>(ctr);
+}
 
-    // Batch b covers list positions [b S, min(b S + S, bmax)), b = nb - 1 .. 0
-    // (the forward's batches, so chunks start at multiples of 32).  The last
-    // goes to buffer 0 now; the list entries of the one before it are loaded
-    // ahead so that its copies issue without waiting.
-    const int nb = (bmax + S - 1) / S;
-    uint32_t rn[RPT];
+// Forward, L1 loss and backward of each tile in one CTA (the pixel-pair
+// tilings): the forward walk and epilogue of k_raster_fwd2 with the L1 target,
+// then the reverse walk of k_raster_bwd2 started from the lanes' registers
+// (final T, last contributors, dL/dC), so that no per-pixel state goes through
+// memory between the two and the backward's record gathers find the records
+// the forward just staged in L2.  T, the last contributors and dL/dC are
+// stored only when their buffers are given.  The forward's cover masks are
+// kept in shared memory for lists of at most kStepMaskChunks(NT) chunks of 32
+// records (128 records at 64 threads); the backward of a longer list repeats
+// its cover passes.  Colour, L1 partials, T, last contributors and dL/dC
+// equal k_raster_fwd2's bit for bit, and every per-record term the backward
+// adds equals k_raster_bwd2's (the sums differ only by the order of the
+// floating-point atomics).
+constexpr int kStepMaskChunks(int nt) { return nt >= 256 ? 1 : 256 / nt; }
+
+template <int TW, int TH, int S, bool PERSIST>
+__global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_threads_per_sm(S))) k_raster_step2(
+    ViewTable vt, RenderOpts ro, const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
+    const uint32_t* __restrict__ ranges, float* __restrict__ color, float* __restrict__ Tout,
+    uint32_t* __restrict__ ncontrib, const int32_t* __restrict__ status, uint32_t* ctr,
+    const uint32_t* __restrict__ order, const float* __restrict__ target, float* __restrict__ dLdC,
+    float* __restrict__ l1_partial, float* __restrict__ grad2d) {
+  using PB = PairBlock<TW>;
+  constexpr int NT = TW * TH / 2, NW = NT / 32;
+  static_assert(pair_tiles(TW, TH) && TH % PB::BH == 0 && NT % 32 == 0, "tile must hold whole pair blocks");
+  __shared__ __align__(16) float4 s_rec[2][S][kRecordF4];
+  __shared__ uint32_t s_ridx[2][S];
+  __shared__ float s_l1[NW];
+  __shared__ float s_tgt[3][2 * NT];   // the pixels' targets, copied in while the tile composites
+  __shared__ uint32_t s_wmax[NW];
+  __shared__ uint32_t s_hm[kStepMaskChunks(NT) * (NT + NW)];   // cover masks, hit-mask slot layout
+  __shared__ int s_item;
+  if (*status != 0) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float t_eps = ro.t_eps, amax = ro.alpha_max;
+  const int my_field = warp_sum10_field(lane);
+  for (int iter = 0;; ++iter) {
+    const int g = next_tile<PERSIST>(iter, vt.total_tiles, ctr, order, &s_item);
+    if (g < 0) break;
+    const int v = view_of_tile(vt, g);
+    const int W = vt.v[v].width, H = vt.v[v].height, ntx = vt.v[v].ntx;
+    const int lt = g - vt.v[v].tile_off;
+    const int ty = lt / ntx, tx = lt - ty * ntx;
+    const int bx = tx * TW + (warp % PB::WX) * PB::BW, by = ty * TH + (warp / PB::WX) * PB::BH;
+    const int x = bx + 2 * (lane % PB::PC), y = by + lane / PB::PC;   // pixels (x, y), (x + 1, y)
+    const bool in0 = x < W && y < H, in1 = x + 1 < W && y < H;
+    const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
+    const uint32_t start = ranges[g], end = ranges[g + 1];
+    uint32_t* const hs = ((end - start + 31u) >> 5) <= (uint32_t)kStepMaskChunks(NT) ? s_hm : nullptr;
     {
-      const int lo0 = (nb - 1) * S, lo1 = lo0 - S;
+      const int64_t HW = (int64_t)W * H;
+      const int64_t o = 3 * vt.v[v].pix_off + (int64_t)y * W + x;
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int jj = tid + q * NT;
-        if (nb > 0 && jj < bmax - lo0) {
-          const uint32_t r = lst[lo0 + jj];
-          s_ridx[0][jj] = r;
-          stage_record(s_rec[0][jj], rec, r);
-        }
-        rn[q] = (lo1 >= 0 && jj < S) ? lst[lo1 + jj] : 0u;
+      for (int ch = 0; ch < 3; ++ch) {
+        if (in0) cp_async4(&s_tgt[ch][2 * tid], target + o + ch * HW);
+        if (in1) cp_async4(&s_tgt[ch][2 * tid + 1], target + o + 1 + ch * HW);
       }
-      cp_async_commit();
     }
+    PairFwdState fs;
+    pair_fwd_walk<TW, TH, S>(s_rec, rec, vals, start, end, hs, xf, yf, bxf, byf, in0, in1, t_eps, amax, fs);
+    float gv[6];
+    const float l1 = pair_fwd_out<NT>(fs, vt, v, x, y, in0, in1, true, s_tgt, color, Tout, ncontrib, dLdC, gv);
+    // also the barrier after which no warp still reads the forward's s_rec
+    // and every cover mask in s_hm is visible to the whole CTA
+    tile_l1_partial<NW>(l1, s_l1, l1_partial + g);
 
-    // hit masks of the next chunk (chunks are walked from the last down),
-    // loaded one chunk ahead so that their DRAM latency overlaps a chunk
-    uint32_t pf_mine = 0u, pf_wide = 0u;
-    int pf_chunk = -1;
-    int buf = 0;
-    for (int b = nb - 1; b >= 0; --b) {
-      const int lo = b * S;
-      const int cnt = min(S, bmax - lo);
-      cp_async_wait_all();
-      __syncthreads();
-      {
-        // copies of batch b - 1 (full) into the other buffer, entries of b - 2
-#pragma unroll
-        for (int q = 0; q < RPT; ++q) {
-          const int jj = tid + q * NT;
-          if (b >= 1 && jj < S) {
-            s_ridx[buf ^ 1][jj] = rn[q];
-            stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
-          }
-          rn[q] = (b >= 2 && jj < S) ? lst[(b - 2) * S + jj] : 0u;
-        }
-        cp_async_commit();
-      }
-      for (int c = ((cnt - 1) >> 5) << 5; c >= 0; c -= 32) {
-        if ((uint32_t)(lo + c) >= wmax) continue;
-        uint32_t wide, mine;
-        if (hslot) {
-          const int j = (lo + c) >> 5;
-          if (pf_chunk == j) {                           // the forward's pass 1
-            mine = pf_mine;
-            wide = pf_wide;
-          } else {
-            const uint32_t* slot = hslot + (size_t)j * (NT + NW);
-            mine = slot[tid];
-            wide = slot[NT + warp];
-          }
-          if (j >= 1) {
-            const uint32_t* nslot = hslot + (size_t)(j - 1) * (NT + NW);
-            pf_mine = nslot[tid];
-            pf_wide = nslot[NT + warp];
-            pf_chunk = j - 1;
-          }
-          const int limw = (int)wmax - (lo + c);         // no lane of the warp reaches past wmax
-          wide &= limw >= 32 ? 0xffffffffu : (1u << limw) - 1u;
-        } else {
-          const int idx = c + lane;
-          const uint32_t cov = (idx < cnt && (uint32_t)(lo + idx) < wmax)
-                                   ? pair_cover<PB::BW>(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
-          wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
-          mine = transpose32(cov, lane);
-        }
-        const int lim = (int)nlm - (lo + c);           // only positions before a pixel's last contributor
-        mine &= lim >= 32 ? 0xffffffffu : (lim <= 0 ? 0u : (1u << lim) - 1u);
-        // pass 2, in reverse list order: between wide records every lane walks
-        // its own records at both of its pixels and adds their summed terms
-        // with three vector atomics; a wide record is done by the whole warp
-        // together (reduce-scatter, one atomic per value)
-        for (;;) {
-          const int kb = wide ? 31 - __clz(wide) : -1;                 // warp-uniform
-          const uint32_t above = kb >= 0 ? ~((2u << kb) - 1u) : 0xffffffffu;
-          uint32_t seg = mine & above;
-          mine &= ~above;
-          while (seg) {
-            const int k = 31 - __clz(seg);
-            seg &= ~(1u << k);
-            const int s = c + k;
-            const uint32_t pos = (uint32_t)(lo + s);
-            const float4 f0 = s_rec[buf][s][0], f1 = s_rec[buf][s][1], f2 = s_rec[buf][s][2];
-            float u0, v0, u1, v1, r2a, r2b;
-            rec_r2_pair(f0, f1, xf, yf, u0, v0, u1, v1, r2a, r2b);
-            float G[kGrad2d];
-            const bool a0 = pix_terms<false>(u0, v0, r2a, f1, f2, amax, pos < nl0, g0x, g0y, g0z, T0, GS0, G);
-            const bool a1 = pix_terms<true>(u1, v1, r2b, f1, f2, amax, pos < nl1, g1x, g1y, g1z, T1, GS1, G);
-            if (!(a0 || a1)) continue;                  // outside the support (the cover is conservative)
-            float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
-            red_add_v4(gdst + 0, G[0], G[1], G[2], G[3]);
-            red_add_v4(gdst + 4, G[4], G[5], G[6], G[7]);
-            red_add_v4(gdst + 8, G[8], G[9], 0.0f, 0.0f);
-          }
-          if (kb < 0) break;
-          wide &= ~(1u << kb);
-          const bool mine_kb = (mine >> kb) & 1u;
-          mine &= ~(1u << kb);
-          const int s = c + kb;
-          const uint32_t pos = (uint32_t)(lo + s);
-          const float4 f0 = s_rec[buf][s][0], f1 = s_rec[buf][s][1], f2 = s_rec[buf][s][2];
-          float u0, v0, u1, v1, r2a, r2b;
-          rec_r2_pair(f0, f1, xf, yf, u0, v0, u1, v1, r2a, r2b);
-          float G[kGrad2d];                              // zero where a pixel is not covered
-          pix_terms<false>(u0, v0, r2a, f1, f2, amax, mine_kb && pos < nl0, g0x, g0y, g0z, T0, GS0, G);
-          pix_terms<true>(u1, v1, r2b, f1, f2, amax, mine_kb && pos < nl1, g1x, g1y, g1z, T1, GS1, G);
-          const float tot = warp_sum10(G, lane);
-          float* gdst = grad2d + (size_t)s_ridx[buf][s] * kGrad2dStride;
-          if (my_field >= 0 && tot != 0.0f) atomicAdd(gdst + my_field, tot);
-        }
-      }
-      buf ^= 1;
-    }
-    cp_async_wait_all();   // no copy may still land in a buffer the next tile fills
-    __syncthreads();
+    const float* bg = vt.v[v].bg;
+    PairBwdState bs;
+    bs.T0 = fs.T0;
+    bs.T1 = fs.T1;
+    bs.g0x = gv[0];
+    bs.g0y = gv[1];
+    bs.g0z = gv[2];
+    bs.g1x = gv[3];
+    bs.g1y = gv[4];
+    bs.g1z = gv[5];
+    bs.nl0 = fs.last0;
+    bs.nl1 = fs.last1;
+    bs.GS0 = in0 ? bs.T0 * (bs.g0x * bg[0] + bs.g0y * bg[1] + bs.g0z * bg[2]) : 0.0f;
+    bs.GS1 = in1 ? bs.T1 * (bs.g1x * bg[0] + bs.g1y * bg[1] + bs.g1z * bg[2]) : 0.0f;
+    pair_bwd_walk<TW, TH, S>(s_rec, s_ridx, s_wmax, rec, vals + start, hs, grad2d, xf, yf, bxf, byf, amax,
+                             my_field, bs);
   }
   leave<PERSIST>(ctr);
 }
@@ -1314,6 +1497,30 @@ cudaError_t bwd_shape(const ViewTable& vt, const RenderOpts& ro, const float4* r
   return cudaGetLastError();
 }
 
+// Forward + L1 + backward in one launch (pixel-pair tilings only).
+template <int TW, int TH, int S>
+cudaError_t step_shape(const ViewTable& vt, const RenderOpts& ro, const float4* rec, const uint32_t* vals,
+                       const uint32_t* ranges, float* color, float* T_final, uint32_t* n_contrib,
+                       const int32_t* status, uint32_t* sched, const float* target, float* dL_dcolor,
+                       float* l1_partial, float* grad2d, cudaStream_t s) {
+  if constexpr (kPairs<TW, TH>) {
+    constexpr int NT = TW * TH / 2;
+    if (sched) {
+      auto k = k_raster_step2<TW, TH, S, true>;
+      k<<<persistent_grid(k, NT, vt.total_tiles), NT, 0, s>>>(
+          vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched + 0, sched + kSchedOrder, target,
+          dL_dcolor, l1_partial, grad2d);
+    } else {
+      k_raster_step2<TW, TH, S, false><<<vt.total_tiles, NT, 0, s>>>(
+          vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, nullptr, nullptr, target, dL_dcolor,
+          l1_partial, grad2d);
+    }
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;   // 8 x 4 tiles have no pixel-pair kernels
+  }
+}
+
 // (tile shape, batch) -> instantiation.  Supported: 8x4 (one warp), 8x8,
 // 16x8, 16x16, 32x16 tiles; batches of 64, 128 or 256 records (at most 8
 // records per thread).
@@ -1376,6 +1583,28 @@ cudaError_t launch_raster_fwd_l1(const ViewTable& vt_in, const RenderOpts& ro, c
     const ViewTable& vt = vt_in;
     BETA_TILE_DISPATCH(fwd_shape, vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched,
                        target, dL_dcolor, ws, hm, s)
+  }();
+  if (e != cudaSuccess) return e;
+  ViewTable vt = vt_in;   // the reduce finds view v's partials from tile_off[v]
+  for (int v = 0; v < vt.n_views; ++v) vt.v[v].pad0 = vt.v[v].tile_off;
+  k_l1_reduce<<<vt.n_views, 256, 0, s>>>(vt, ws, vt.total_tiles, loss);
+  return cudaGetLastError();
+}
+
+bool raster_step_supported(const RenderOpts& ro) { return pair_tiles(ro.tile_w, ro.tile_h); }
+
+// Forward, L1 loss and backward in one launch; k_l1_reduce then sums each
+// view's tile partials in order, as launch_raster_fwd_l1 does.
+cudaError_t launch_raster_step_l1(const ViewTable& vt_in, const RenderOpts& ro, const float4* rec,
+                                  const uint32_t* vals, const uint32_t* ranges, float* color, float* T_final,
+                                  uint32_t* n_contrib, const int32_t* status, uint32_t* sched, const float* target,
+                                  float* loss, float* dL_dcolor, float* ws, float* grad2d, cudaStream_t s) {
+  if (vt_in.total_tiles <= 0) return cudaSuccess;
+  if (!raster_step_supported(ro)) return cudaErrorInvalidValue;
+  cudaError_t e = [&]() -> cudaError_t {
+    const ViewTable& vt = vt_in;
+    BETA_TILE_DISPATCH(step_shape, vt, ro, rec, vals, ranges, color, T_final, n_contrib, status, sched, target,
+                       dL_dcolor, ws, grad2d, s)
   }();
   if (e != cudaSuccess) return e;
   ViewTable vt = vt_in;   // the reduce finds view v's partials from tile_off[v]

@@ -173,6 +173,27 @@ class Rasterizer:
             _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), hm, hb, _vp(self.T_final),
             _vp(self.n_contrib), _vp(dL_dcolor), _vp(self.grad2d), _vp(self.status), _stream()))
 
+    @property
+    def fused_supported(self) -> bool:
+        """Whether raster_fwd_bwd_l1 serves this tile shape: every shape whose
+        raster kernels give a thread two pixels, i.e. all but 8x4 tiles."""
+        return (int(self.opts.tile_w), int(self.opts.tile_h)) != (8, 4)
+
+    def raster_fwd_bwd_l1(self, planes, target: torch.Tensor, keep_state: bool = False):
+        """raster_fwd_l1 followed by raster_bwd of its dL/dC, in one launch
+        (each tile's CTA composites, forms the L1 term and walks back from its
+        registers): colour, per-view loss and the 2D-gradient sums.  With
+        keep_state T_final, n_contrib and dL_dcolor are written as well."""
+        assert target.numel() == self.color.numel() and target.is_contiguous()
+        prm = self.params(planes)
+        keep = (lambda t: _vp(t)) if keep_state else (lambda t: ctypes.c_void_p(0))
+        _lib.check("beta_raster_fwd_bwd_l1", self.L.beta_raster_fwd_bwd_l1(
+            ctypes.byref(prm), self.cams, self.V, ctypes.byref(self.opts), _vp(self.proj),
+            _vp(self.pair_vals), _vp(self.ranges), _vp(self.sched), _vp(self.color), keep(self.T_final),
+            keep(self.n_contrib), _vp(target), _vp(self.loss), keep(self.dL_dcolor), _vp(self.grad2d),
+            _vp(self.fwd_l1_ws), self.fwd_l1_ws.numel(), _vp(self.status), _stream()))
+        return self.loss
+
     def project_bwd(self, planes, grad_planes, c0: int = 0, c1: int | None = None):
         """Raw-parameter gradients of primitives [c0, c1) (all by default): the
         same entry point on the primitive range, through pointers offset by c0

@@ -517,3 +517,57 @@ def test_forward_with_fused_l1_equals_separate_calls(tile, persistent):
     assert torch.equal(d_b, d_a)
     la, lb = loss_a.cpu().numpy().astype(np.float64), loss_b.cpu().numpy().astype(np.float64)
     assert np.all(la > 0) and np.max(np.abs(la - lb) / la) < 1e-5
+
+
+@pytest.mark.parametrize("tile,bs,persistent", [((16, 8), 64, False), ((16, 8), 128, True), ((8, 8), 64, False),
+                                                ((16, 16), 256, True), ((32, 16), 128, False)])
+def test_forward_backward_in_one_launch_equals_separate_calls(tile, bs, persistent):
+    """beta_raster_fwd_bwd_l1 = beta_raster_fwd_l1 then beta_raster_bwd of
+    its dL/dC: image, T, n_contrib and dL/dC bit for bit, the per-view loss
+    bit for bit (the same tile partials summed in the same order), and the
+    2D-gradient sums within 1e-5 of each field's largest value (the same
+    terms, added by atomics in another order).  Without the optional state
+    buffers the image, loss and gradients are the same.  8x4 tiles, which
+    have no pixel-pair kernels, are refused."""
+    sc = scenes.config_scene(4, n=40_000, n_views=8)
+    cams = sc.cameras[::2]                                  # four sizes, ragged edge tiles
+    opts = _lib.default_opts(tile_w=tile[0], tile_h=tile[1], batch_s=bs)
+    gc.ensure_built()
+    planes = torch.from_numpy(np.ascontiguousarray(sc.planes)).cuda()
+    target = torch.from_numpy(np.concatenate([t.reshape(-1) for t in scenes.target_images(cams, seed=7)])).cuda()
+    rast = render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, cams, opts, persistent=persistent)
+    rast.forward(planes)
+    if persistent:
+        rast.schedule()
+    loss_a, d_a = (x.clone() for x in rast.raster_fwd_l1(planes, target))
+    img_a, T_a, n_a = rast.color.clone(), rast.T_final.clone(), rast.n_contrib.clone()
+    rast.raster_bwd(planes, rast.dL_dcolor)
+    g2_a = rast.grad2d.clone()
+    rast.grad2d.zero_()
+    out = []
+    for keep in (True, False):
+        rast.color.zero_(); rast.T_final.zero_(); rast.n_contrib.zero_(); rast.dL_dcolor.zero_()
+        rast.loss.zero_(); rast.grad2d.zero_()
+        if persistent:
+            rast.schedule()
+        rast.raster_fwd_bwd_l1(planes, target, keep_state=keep)
+        torch.cuda.synchronize()
+        out.append((rast.color.clone(), rast.loss.clone(), rast.grad2d.clone(), rast.T_final.clone(),
+                    rast.n_contrib.clone(), rast.dL_dcolor.clone()))
+    g_ref = g2_a.view(-1, 12)[:, :10].cpu().numpy().astype(np.float64)
+    scale = np.abs(g_ref).max(axis=0) + 1e-30
+    assert np.all(np.abs(g_ref).max(axis=0) > 0)
+    for k, (img, loss, g2, T, nc, d) in enumerate(out):
+        assert torch.equal(img, img_a) and torch.equal(loss, loss_a)
+        g = g2.view(-1, 12)[:, :10].cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(g - g_ref) / scale) < 1e-5
+        assert bool((g2.view(-1, 12)[:, 10:] == 0).all())
+        if k == 0:
+            assert torch.equal(T, T_a) and torch.equal(nc, n_a) and torch.equal(d, d_a)
+        else:                                               # not written without their buffers
+            assert bool((T == 0).all()) and bool((nc == 0).all()) and bool((d == 0).all())
+    r84 = render.Rasterizer(sc.n, sc.pitch, sc.n_lobes, cams, _lib.default_opts(tile_w=8, tile_h=4))
+    assert not r84.fused_supported
+    with pytest.raises(_lib.BetaError) as e:
+        r84.raster_fwd_bwd_l1(planes, target)
+    assert e.value.code == _lib.BETA_ERR_ARG
