@@ -1,7 +1,8 @@
 """Full-size workloads beyond the benchmark's: 3M Betas over views of mixed
 resolution, and 6M Betas over eight 3840x2160 views in one captured step
-under a stated HBM budget (24 GB, hit masks included; the backward
-recomputes alpha rather than storing it)."""
+under a stated HBM budget (24 GB; the backward recomputes alpha rather than
+storing it).  The captured steps run the raster forward, L1 loss and
+backward in one launch per tile, as the benchmark does."""
 import numpy as np
 import pytest
 import torch
@@ -52,8 +53,9 @@ def test_6m_betas_eight_4k_views_in_budget():
 
 def test_1m_betas_sixteen_views_benchmark_configuration():
     """The benchmark's own step: 1M Betas, 16 ring views of 1920x1080, 16x8
-    tiles, 64-record batches, one CTA per tile (the autotuner's pick, pixel-pair
-    raster kernels), captured and replayed.  Two
+    tiles, 64-record batches, one CTA per tile (the autotuner's pick, the
+    one-launch pixel-pair raster forward + L1 + backward), captured and
+    replayed.  Two
     views' binning equals the oracle's bit for bit (a view's lists are the
     view's own); sampled pixels of two views (including whole tiles) equal
     the FP64 oracle; the loss and gradients are finite."""
