@@ -59,8 +59,8 @@ def parse():
     ap.add_argument("--workload", type=int, default=3, choices=[3, 4, 5],
                     help="scene recipe: 3 = 1M Betas (default), 4 = 3M Betas, 5 = 6M Betas")
     ap.add_argument("--raster", choices=["fused", "split"], default="fused",
-                    help="raster forward + L1 + backward in one launch per tile (fused), or as two launches "
-                         "(split); 8x4 tiles always split")
+                    help="fused: the autotuner (or --config) may run the raster forward + L1 + backward in one "
+                         "launch per tile; split: always two launches (8x4 tiles always split)")
     ap.add_argument("--hit-masks", choices=["on", "off"], default="on",
                     help="the forward keeps its cover pass for the backward (on), or the backward recomputes "
                          "it (off)")
@@ -322,18 +322,18 @@ def main():
     if args.config:
         shape, bsz, mode = args.config.split("/")
         tw_, th_ = (int(x) for x in shape.split("x"))
-        best, tune_ms = (tw_, th_, int(bsz), mode.upper() == "P"), {}
+        best, tune_ms = (tw_, th_, int(bsz), mode.upper() == "P", args.raster == "fused"), {}
     else:
         best, tune_ms = autotune.tune(planes, sc.n, sc.n_lobes, cams, target, reps=3, hit_masks=hit_masks,
                                       fused=args.raster == "fused",
                                       log=(lambda m: print(m, file=sys.stderr)) if rank == 0 else None)
     t_tune = time.perf_counter() - t_tune
-    tw, th, bs, persist = best
+    tw, th, bs, persist = best[:4]
     opts = _lib.default_opts(tile_w=tw, tile_h=th, batch_s=bs)
     # on several GPUs the projection backward runs after the replay in chunks,
     # each chunk's gradient all-reduce overlapping the next chunks
     bstep = batched.BatchedStep(planes, sc.n, sc.n_lobes, cams, target, opts=opts, persistent=persist,
-                                hit_masks=hit_masks, graph_project_bwd=world == 1, fused=args.raster == "fused")
+                                hit_masks=hit_masks, graph_project_bwd=world == 1, fused=autotune.fused_of(best))
     rast = bstep.rast
     grad = bstep.grad
 
@@ -651,8 +651,10 @@ def main():
                    "tile": f"{tw}x{th}", "batch_s": bs, "persistent": persist,
                    "raster": "one launch (forward + L1 + backward)" if fused else "forward + L1, backward",
                    "hit_masks": hit_masks and not fused,
-                   "autotune": {"s": round(t_tune, 1), "ms": {f"{c[0]}x{c[1]}/S{c[2]}/{'P' if c[3] else 'G'}": round(v, 3)
-                                                              for c, v in tune_ms.items()}},
+                   "autotune": {"s": round(t_tune, 1),
+                                "ms": {f"{c[0]}x{c[1]}/S{c[2]}/{'P' if c[3] else 'G'}"
+                                       f"{'' if autotune.fused_of(c) else '/split'}": round(v, 3)
+                                       for c, v in tune_ms.items()}},
                    "n_betas": sc.n, "views_per_gpu": V, "resolution": scenes.describe_sizes(cams),
                    "pairs_per_step": K, "l2": f"inputs larger than L2: {sc.n * n_planes * 4 / 1e6:.0f} MB params + "
                                                f"{V * sc.pitch * 64 / 1e6:.0f} MB records per step",

@@ -41,6 +41,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "beta_internal.cuh"
 
@@ -742,13 +743,15 @@ struct PairFwdState {
 // batch loaded one batch ahead); per 32-record chunk the warp's cover pass and
 // bit transpose, then every lane composites its records in list order at both
 // pixels (Eq. C), until T < t_eps at every pixel of the CTA.  With hslot the
-// chunks' cover masks are stored for the backward.  Returns with every copy
-// landed; the caller synchronises the CTA before s_rec is staged again.
+// cover masks of the list's first hm_chunks chunks are stored for the
+// backward.  Returns with every copy landed; the caller synchronises the CTA
+// before s_rec is staged again.
 template <int TW, int TH, int S>
 __device__ __forceinline__ void pair_fwd_walk(float4 (&s_rec)[2][S][kRecordF4], const float4* __restrict__ rec,
                                               const uint32_t* __restrict__ vals, uint32_t start, uint32_t end,
-                                              uint32_t* hslot, float xf, float yf, float bxf, float byf, bool in0,
-                                              bool in1, float t_eps, float amax, PairFwdState& st) {
+                                              uint32_t* hslot, int hm_chunks, float xf, float yf, float bxf,
+                                              float byf, bool in0, bool in1, float t_eps, float amax,
+                                              PairFwdState& st) {
   using PB = PairBlock<TW>;
   constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -791,8 +794,9 @@ __device__ __forceinline__ void pair_fwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
       const uint32_t cov =
           idx < cnt ? pair_cover<PB::BW>(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
       uint32_t mine = transpose32(cov, lane);
-      if (hslot) {
-        uint32_t* slot = hslot + (size_t)((base - start + c) >> 5) * (NT + NW);
+      const int jc = (int)((base - start + c) >> 5);
+      if (hslot && jc < hm_chunks) {
+        uint32_t* slot = hslot + (size_t)jc * (NT + NW);
         const uint32_t wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
         slot[tid] = mine;
         if (lane == 0) slot[NT + warp] = wide;
@@ -956,8 +960,8 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
       }
     }
     PairFwdState fs;
-    pair_fwd_walk<TW, TH, S>(s_rec, rec, vals, start, end, hslot, (float)x, (float)y, (float)bx, (float)by, in0,
-                             in1, t_eps, amax, fs);
+    pair_fwd_walk<TW, TH, S>(s_rec, rec, vals, start, end, hslot, INT_MAX, (float)x, (float)y, (float)bx,
+                             (float)by, in0, in1, t_eps, amax, fs);
     float gv[6];
     const float l1 = pair_fwd_out<NT>(fs, vt, v, x, y, in0, in1, target != nullptr, s_tgt, color, Tout, ncontrib,
                                       dLdC, gv);
@@ -1006,7 +1010,8 @@ struct PairBwdState {
 // largest last-contributor position down: batches of S records staged as the
 // forward staged them (so chunks start at multiples of 32), the list entries
 // of the next batch down loaded one batch ahead; per chunk the cover masks
-// (the forward's from hslot, else the cover pass again), then every lane's
+// (the forward's from hslot for the list's first hm_chunks chunks, else the
+// cover pass again), then every lane's
 // walk of its records in reverse list order at both pixels with three vector
 // atomics per record, and records covering more than kLaneAtomics of the
 // warp's pairs by the whole warp (reduce-scatter, one atomic per value).
@@ -1015,8 +1020,9 @@ template <int TW, int TH, int S>
 __device__ __forceinline__ void pair_bwd_walk(float4 (&s_rec)[2][S][kRecordF4], uint32_t (&s_ridx)[2][S],
                                               uint32_t (&s_wmax)[TW * TH / 64], const float4* __restrict__ rec,
                                               const uint32_t* __restrict__ lst, const uint32_t* hslot,
-                                              float* __restrict__ grad2d, float xf, float yf, float bxf, float byf,
-                                              float amax, int my_field, const PairBwdState& st) {
+                                              int hm_chunks, float* __restrict__ grad2d, float xf, float yf,
+                                              float bxf, float byf, float amax, int my_field,
+                                              const PairBwdState& st) {
   using PB = PairBlock<TW>;
   constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1078,8 +1084,8 @@ __device__ __forceinline__ void pair_bwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
     for (int c = ((cnt - 1) >> 5) << 5; c >= 0; c -= 32) {
       if ((uint32_t)(lo + c) >= wmax) continue;
       uint32_t wide, mine;
-      if (hslot) {
-        const int j = (lo + c) >> 5;
+      const int j = (lo + c) >> 5;
+      if (hslot && j < hm_chunks) {
         if (pf_chunk == j) {                           // the forward's pass 1
           mine = pf_mine;
           wide = pf_wide;
@@ -1087,12 +1093,6 @@ __device__ __forceinline__ void pair_bwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
           const uint32_t* slot = hslot + (size_t)j * (NT + NW);
           mine = slot[tid];
           wide = slot[NT + warp];
-        }
-        if (j >= 1) {
-          const uint32_t* nslot = hslot + (size_t)(j - 1) * (NT + NW);
-          pf_mine = nslot[tid];
-          pf_wide = nslot[NT + warp];
-          pf_chunk = j - 1;
         }
         const int limw = (int)wmax - (lo + c);         // no lane of the warp reaches past wmax
         wide &= limw >= 32 ? 0xffffffffu : (1u << limw) - 1u;
@@ -1102,6 +1102,12 @@ __device__ __forceinline__ void pair_bwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
                                  ? pair_cover<PB::BW>(s_rec[buf][idx][0], s_rec[buf][idx][1], bxf, byf) : 0u;
         wide = __ballot_sync(0xffffffffu, __popc(cov) > kLaneAtomics);
         mine = transpose32(cov, lane);
+      }
+      if (hslot && j >= 1 && j - 1 < hm_chunks) {     // the next chunk's stored masks, one chunk ahead
+        const uint32_t* nslot = hslot + (size_t)(j - 1) * (NT + NW);
+        pf_mine = nslot[tid];
+        pf_wide = nslot[NT + warp];
+        pf_chunk = j - 1;
       }
       const int lim = (int)nlm - (lo + c);           // only positions before a pixel's last contributor
       mine &= lim >= 32 ? 0xffffffffu : (lim <= 0 ? 0u : (1u << lim) - 1u);
@@ -1207,7 +1213,7 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
         bs.GS1 = bs.T1 * (bs.g1x * bg[0] + bs.g1y * bg[1] + bs.g1z * bg[2]);
       }
     }
-    pair_bwd_walk<TW, TH, S>(s_rec, s_ridx, s_wmax, rec, vals + range0, hslot, grad2d, (float)x, (float)y,
+    pair_bwd_walk<TW, TH, S>(s_rec, s_ridx, s_wmax, rec, vals + range0, hslot, INT_MAX, grad2d, (float)x, (float)y,
                              (float)bx, (float)by, amax, my_field, bs);
   }
   leave<PERSIST>(ctr);
@@ -1219,14 +1225,14 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
 // (final T, last contributors, dL/dC), so that no per-pixel state goes through
 // memory between the two and the backward's record gathers find the records
 // the forward just staged in L2.  T, the last contributors and dL/dC are
-// stored only when their buffers are given.  The forward's cover masks are
-// kept in shared memory for lists of at most kStepMaskChunks(NT) chunks of 32
-// records (128 records at 64 threads); the backward of a longer list repeats
-// its cover passes.  Colour, L1 partials, T, last contributors and dL/dC
+// stored only when their buffers are given.  The forward's cover masks of
+// each list's first kStepMaskChunks(NT) chunks of 32 records (192 records at
+// 64 threads, 1.5 KB) are kept in shared memory; the backward repeats the
+// cover passes of later chunks.  Colour, L1 partials, T, last contributors and dL/dC
 // equal k_raster_fwd2's bit for bit, and every per-record term the backward
 // adds equals k_raster_bwd2's (the sums differ only by the order of the
 // floating-point atomics).
-constexpr int kStepMaskChunks(int nt) { return nt >= 256 ? 1 : 256 / nt; }
+constexpr int kStepMaskChunks(int nt) { return nt >= 384 ? 1 : 384 / nt; }
 
 template <int TW, int TH, int S, bool PERSIST>
 __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_threads_per_sm(S))) k_raster_step2(
@@ -1261,7 +1267,6 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
     const bool in0 = x < W && y < H, in1 = x + 1 < W && y < H;
     const float xf = (float)x, yf = (float)y, bxf = (float)bx, byf = (float)by;
     const uint32_t start = ranges[g], end = ranges[g + 1];
-    uint32_t* const hs = ((end - start + 31u) >> 5) <= (uint32_t)kStepMaskChunks(NT) ? s_hm : nullptr;
     {
       const int64_t HW = (int64_t)W * H;
       const int64_t o = 3 * vt.v[v].pix_off + (int64_t)y * W + x;
@@ -1272,7 +1277,8 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
       }
     }
     PairFwdState fs;
-    pair_fwd_walk<TW, TH, S>(s_rec, rec, vals, start, end, hs, xf, yf, bxf, byf, in0, in1, t_eps, amax, fs);
+    pair_fwd_walk<TW, TH, S>(s_rec, rec, vals, start, end, s_hm, kStepMaskChunks(NT), xf, yf, bxf, byf, in0, in1,
+                             t_eps, amax, fs);
     float gv[6];
     const float l1 = pair_fwd_out<NT>(fs, vt, v, x, y, in0, in1, true, s_tgt, color, Tout, ncontrib, dLdC, gv);
     // also the barrier after which no warp still reads the forward's s_rec
@@ -1293,8 +1299,8 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
     bs.nl1 = fs.last1;
     bs.GS0 = in0 ? bs.T0 * (bs.g0x * bg[0] + bs.g0y * bg[1] + bs.g0z * bg[2]) : 0.0f;
     bs.GS1 = in1 ? bs.T1 * (bs.g1x * bg[0] + bs.g1y * bg[1] + bs.g1z * bg[2]) : 0.0f;
-    pair_bwd_walk<TW, TH, S>(s_rec, s_ridx, s_wmax, rec, vals + start, hs, grad2d, xf, yf, bxf, byf, amax,
-                             my_field, bs);
+    pair_bwd_walk<TW, TH, S>(s_rec, s_ridx, s_wmax, rec, vals + start, s_hm, kStepMaskChunks(NT), grad2d, xf, yf,
+                             bxf, byf, amax, my_field, bs);
   }
   leave<PERSIST>(ctr);
 }
