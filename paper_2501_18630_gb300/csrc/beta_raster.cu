@@ -735,6 +735,7 @@ __device__ __forceinline__ void rec_r2_pair(float4 f0, float4 f1, float xf, floa
 struct PairFwdState {
   float T0, T1, C00, C01, C02, C10, C11, C12;
   uint32_t last0, last1;
+  int walked_batch, walked_buf;   // the last batch the walk composited and its s_rec buffer (-1: none)
 };
 
 // Forward walk of one tile's list [start, end) at the lane's pixel pair (xf,
@@ -744,14 +745,16 @@ struct PairFwdState {
 // bit transpose, then every lane composites its records in list order at both
 // pixels (Eq. C), until T < t_eps at every pixel of the CTA.  With hslot the
 // cover masks of the list's first hm_chunks chunks are stored for the
-// backward.  Returns with every copy landed; the caller synchronises the CTA
-// before s_rec is staged again.
+// backward; with ridx (a [2][S] array) the staged records' indices as well,
+// so that a backward can start from the last batch still in s_rec.  Returns
+// with every copy landed; the caller synchronises the CTA before s_rec is
+// staged again.
 template <int TW, int TH, int S>
-__device__ __forceinline__ void pair_fwd_walk(float4 (&s_rec)[2][S][kRecordF4], const float4* __restrict__ rec,
-                                              const uint32_t* __restrict__ vals, uint32_t start, uint32_t end,
-                                              uint32_t* hslot, int hm_chunks, float xf, float yf, float bxf,
-                                              float byf, bool in0, bool in1, float t_eps, float amax,
-                                              PairFwdState& st) {
+__device__ __forceinline__ void pair_fwd_walk(float4 (&s_rec)[2][S][kRecordF4], uint32_t* ridx,
+                                              const float4* __restrict__ rec, const uint32_t* __restrict__ vals,
+                                              uint32_t start, uint32_t end, uint32_t* hslot, int hm_chunks,
+                                              float xf, float yf, float bxf, float byf, bool in0, bool in1,
+                                              float t_eps, float amax, PairFwdState& st) {
   using PB = PairBlock<TW>;
   constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -762,7 +765,11 @@ __device__ __forceinline__ void pair_fwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
 #pragma unroll
   for (int q = 0; q < RPT; ++q) {
     const int jj = tid + q * NT;
-    if (jj < S && start + jj < end) stage_record(s_rec[0][jj], rec, vals[start + jj]);
+    if (jj < S && start + jj < end) {
+      const uint32_t r = vals[start + jj];
+      if (ridx) ridx[jj] = r;
+      stage_record(s_rec[0][jj], rec, r);
+    }
     const uint32_t j1 = start + S + jj;
     rn[q] = (jj < S && j1 < end) ? vals[j1] : 0u;
   }
@@ -773,19 +780,24 @@ __device__ __forceinline__ void pair_fwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
   bool done0 = !in0, done1 = !in1;
   bool warp_done = __all_sync(0xffffffffu, done0 && done1);
 
-  int buf = 0;
-  for (uint32_t base = start; base < end; base += S) {
+  int buf = 0, batch = 0, walked_batch = -1, walked_buf = -1;
+  for (uint32_t base = start; base < end; base += S, ++batch) {
     cp_async_wait_all();
     if (!__syncthreads_or(!(done0 && done1))) break;
     const uint32_t nb = base + S;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       const int jj = tid + q * NT;
-      if (jj < S && nb + jj < end) stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
+      if (jj < S && nb + jj < end) {
+        if (ridx) ridx[(buf ^ 1) * S + jj] = rn[q];
+        stage_record(s_rec[buf ^ 1][jj], rec, rn[q]);
+      }
       const uint32_t j2 = nb + S + jj;
       rn[q] = (jj < S && j2 < end) ? vals[j2] : 0u;
     }
     cp_async_commit();
+    walked_batch = batch;
+    walked_buf = buf;
     const int cnt = (int)min((uint32_t)S, end - base);
     for (int c = 0; c < cnt && !warp_done; c += 32) {
       // pass 1: lane k finds the pairs of this warp's block that record
@@ -853,6 +865,8 @@ __device__ __forceinline__ void pair_fwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
   st.C12 = C12;
   st.last0 = last0;
   st.last1 = last1;
+  st.walked_batch = walked_batch;
+  st.walked_buf = walked_buf;
 }
 
 // Epilogue of the pixel-pair forward at pixels (x, y), (x + 1, y) of view v:
@@ -960,7 +974,7 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
       }
     }
     PairFwdState fs;
-    pair_fwd_walk<TW, TH, S>(s_rec, rec, vals, start, end, hslot, INT_MAX, (float)x, (float)y, (float)bx,
+    pair_fwd_walk<TW, TH, S>(s_rec, nullptr, rec, vals, start, end, hslot, INT_MAX, (float)x, (float)y, (float)bx,
                              (float)by, in0, in1, t_eps, amax, fs);
     float gv[6];
     const float l1 = pair_fwd_out<NT>(fs, vt, v, x, y, in0, in1, target != nullptr, s_tgt, color, Tout, ncontrib,
@@ -1015,6 +1029,9 @@ struct PairBwdState {
 // walk of its records in reverse list order at both pixels with three vector
 // atomics per record, and records covering more than kLaneAtomics of the
 // warp's pairs by the whole warp (reduce-scatter, one atomic per value).
+// When the first batch it needs is reuse_batch, which a forward walk left
+// complete in s_rec[reuse_buf] with its indices in s_ridx[reuse_buf], it
+// starts from there instead of staging it again (reuse_batch = -1: never).
 // Returns with every copy landed and the CTA synchronised.
 template <int TW, int TH, int S>
 __device__ __forceinline__ void pair_bwd_walk(float4 (&s_rec)[2][S][kRecordF4], uint32_t (&s_ridx)[2][S],
@@ -1022,7 +1039,7 @@ __device__ __forceinline__ void pair_bwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
                                               const uint32_t* __restrict__ lst, const uint32_t* hslot,
                                               int hm_chunks, float* __restrict__ grad2d, float xf, float yf,
                                               float bxf, float byf, float amax, int my_field,
-                                              const PairBwdState& st) {
+                                              const PairBwdState& st, int reuse_batch, int reuse_buf) {
   using PB = PairBlock<TW>;
   constexpr int NT = TW * TH / 2, NW = NT / 32, RPT = (S + NT - 1) / NT;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1039,16 +1056,19 @@ __device__ __forceinline__ void pair_bwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
 
   // Batch b covers list positions [b S, min(b S + S, bmax)), b = nb - 1 .. 0
   // (the forward's batches, so chunks start at multiples of 32).  The last
-  // goes to buffer 0 now; the list entries of the one before it are loaded
-  // ahead so that its copies issue without waiting.
+  // goes to buffer 0 now (or is already in reuse_buf); the list entries of
+  // the one before it are loaded ahead so that its copies issue without
+  // waiting.
   const int nb = (bmax + S - 1) / S;
+  const bool reuse = nb > 0 && reuse_batch == nb - 1;   // CTA-uniform
+  int buf = reuse ? reuse_buf : 0;
   uint32_t rn[RPT];
   {
     const int lo0 = (nb - 1) * S, lo1 = lo0 - S;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       const int jj = tid + q * NT;
-      if (nb > 0 && jj < bmax - lo0) {
+      if (!reuse && nb > 0 && jj < bmax - lo0) {
         const uint32_t r = lst[lo0 + jj];
         s_ridx[0][jj] = r;
         stage_record(s_rec[0][jj], rec, r);
@@ -1062,7 +1082,6 @@ __device__ __forceinline__ void pair_bwd_walk(float4 (&s_rec)[2][S][kRecordF4], 
   // loaded one chunk ahead so that their DRAM latency overlaps a chunk
   uint32_t pf_mine = 0u, pf_wide = 0u;
   int pf_chunk = -1;
-  int buf = 0;
   for (int b = nb - 1; b >= 0; --b) {
     const int lo = b * S;
     const int cnt = min(S, bmax - lo);
@@ -1214,7 +1233,7 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
       }
     }
     pair_bwd_walk<TW, TH, S>(s_rec, s_ridx, s_wmax, rec, vals + range0, hslot, INT_MAX, grad2d, (float)x, (float)y,
-                             (float)bx, (float)by, amax, my_field, bs);
+                             (float)bx, (float)by, amax, my_field, bs, -1, 0);
   }
   leave<PERSIST>(ctr);
 }
@@ -1277,8 +1296,8 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
       }
     }
     PairFwdState fs;
-    pair_fwd_walk<TW, TH, S>(s_rec, rec, vals, start, end, s_hm, kStepMaskChunks(NT), xf, yf, bxf, byf, in0, in1,
-                             t_eps, amax, fs);
+    pair_fwd_walk<TW, TH, S>(s_rec, &s_ridx[0][0], rec, vals, start, end, s_hm, kStepMaskChunks(NT), xf, yf, bxf,
+                             byf, in0, in1, t_eps, amax, fs);
     float gv[6];
     const float l1 = pair_fwd_out<NT>(fs, vt, v, x, y, in0, in1, true, s_tgt, color, Tout, ncontrib, dLdC, gv);
     // also the barrier after which no warp still reads the forward's s_rec
@@ -1300,7 +1319,7 @@ __global__ void __launch_bounds__(TW * TH / 2, min_blocks(TW * TH / 2, pair_thre
     bs.GS0 = in0 ? bs.T0 * (bs.g0x * bg[0] + bs.g0y * bg[1] + bs.g0z * bg[2]) : 0.0f;
     bs.GS1 = in1 ? bs.T1 * (bs.g1x * bg[0] + bs.g1y * bg[1] + bs.g1z * bg[2]) : 0.0f;
     pair_bwd_walk<TW, TH, S>(s_rec, s_ridx, s_wmax, rec, vals + start, s_hm, kStepMaskChunks(NT), grad2d, xf, yf,
-                             bxf, byf, amax, my_field, bs);
+                             bxf, byf, amax, my_field, bs, fs.walked_batch, fs.walked_buf);
   }
   leave<PERSIST>(ctr);
 }
