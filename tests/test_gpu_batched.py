@@ -136,13 +136,17 @@ def test_autotuner_times_candidates_and_caches(tmp_path, monkeypatch):
     gc.ensure_built()
     planes = torch.from_numpy(sc.planes).cuda()
     tgt = torch.from_numpy(scenes.target_images(cams, seed=3)[0].reshape(-1)).cuda()
-    cands = [(16, 16, 256, True), (16, 8, 64, False)]
+    # the last candidate runs the raster forward and backward as two launches
+    cands = [(16, 16, 256, True), (16, 8, 64, False), (16, 8, 64, False, False)]
     best, times = autotune.tune(planes, sc.n, sc.n_lobes, cams, tgt, candidates=cands, reps=2)
     assert best in cands and set(times) == set(cands) and all(t > 0 for t in times.values())
     d = json.load(open(tmp_path / "tune.json"))
     assert len(d) == 1 and list(d.values())[0]["best"] == list(best)
     best2, _ = autotune.tune(planes, sc.n, sc.n_lobes, cams, tgt, candidates=cands)
     assert best2 == best
+    # restricted to two launches, every candidate is timed that way
+    _, t3 = autotune.tune(planes, sc.n, sc.n_lobes, cams, tgt, candidates=cands[:2], reps=1, fused=False)
+    assert set(t3) == {(16, 16, 256, True, False), (16, 8, 64, False, False)}
 
 
 def test_view_split_gradients_sum_to_full_batch():
