@@ -317,6 +317,10 @@ int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
  * tiles (run beta_raster_fwd_l1 and beta_raster_bwd there), for null
  * required pointers and a grad2d that is not 16-byte aligned;
  * BETA_ERR_WORKSPACE for a short or misaligned ws. */
+/* 1 if beta_raster_fwd_bwd_l1 serves these options (valid options whose tile
+ * shape has pixel-pair raster kernels: every supported shape but 8 x 4), else
+ * 0.  Host-only; needs no GPU. */
+int beta_raster_fwd_bwd_l1_supported(const beta_opts* opt /* host */);
 int beta_raster_fwd_bwd_l1(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                            const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
                            const uint32_t* tile_ranges, void* sched, float* color, float* T_final,

@@ -49,7 +49,7 @@ EXPORTS = [
     "beta_schedule", "beta_adam_default_opts", "beta_adam_step", "beta_relocate_workspace_bytes",
     "beta_relocate", "beta_dssim_workspace_bytes", "beta_l1_dssim_loss",
     "beta_raster_fwd_l1_workspace_bytes", "beta_raster_fwd_l1", "beta_debug_scan_faults",
-    "beta_hit_mask_bytes", "beta_raster_fwd_bwd_l1",
+    "beta_hit_mask_bytes", "beta_raster_fwd_bwd_l1", "beta_raster_fwd_bwd_l1_supported",
 ]
 
 
@@ -125,6 +125,7 @@ def load(path: str = LIB_PATH):
             "beta_raster_bwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, sz, vp, vp, vp, vp, vp, vp]),
             "beta_raster_fwd_bwd_l1": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                                       vp, vp, sz, vp, vp]),
+            "beta_raster_fwd_bwd_l1_supported": (ctypes.c_int, [O]),
             "beta_schedule_bytes": (sz, [C, i32, O]),
             "beta_schedule": (ctypes.c_int, [C, i32, O, vp, vp, vp, vp]),
             "beta_project_bwd": (ctypes.c_int, [P, C, i32, O, vp, vp, vp, vp]),

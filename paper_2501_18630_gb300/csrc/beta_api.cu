@@ -369,6 +369,10 @@ int beta_raster_bwd(const beta_params* prm, const beta_camera* cams, int32_t n_v
                                        (uint32_t*)sched, hm, (cudaStream_t)stream));
 }
 
+int beta_raster_fwd_bwd_l1_supported(const beta_opts* opt) {
+  return check_opts(opt) == BETA_OK && raster_step_supported(render_opts(opt)) ? 1 : 0;
+}
+
 int beta_raster_fwd_bwd_l1(const beta_params* prm, const beta_camera* cams, int32_t n_views,
                            const beta_opts* opt, const void* proj, const uint32_t* pair_vals,
                            const uint32_t* tile_ranges, void* sched, float* color, float* T_final,

@@ -175,9 +175,9 @@ class Rasterizer:
 
     @property
     def fused_supported(self) -> bool:
-        """Whether raster_fwd_bwd_l1 serves this tile shape: every shape whose
-        raster kernels give a thread two pixels, i.e. all but 8x4 tiles."""
-        return (int(self.opts.tile_w), int(self.opts.tile_h)) != (8, 4)
+        """Whether raster_fwd_bwd_l1 serves these options: every tile shape
+        whose raster kernels give a thread two pixels, i.e. all but 8x4."""
+        return bool(self.L.beta_raster_fwd_bwd_l1_supported(ctypes.byref(self.opts)))
 
     def raster_fwd_bwd_l1(self, planes, target: torch.Tensor, keep_state: bool = False):
         """raster_fwd_l1 followed by raster_bwd of its dL/dC, in one launch

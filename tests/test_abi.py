@@ -151,3 +151,26 @@ def test_static_scratch_size_matches_header():
     src = open(os.path.join(ROOT, "include", "beta_splat.h")).read()
     m = re.search(r"#define\s+BETA_STATIC_SCRATCH_BYTES\s+\((\d+)u \* (\d+)u \* (\d+)u\)", src)
     assert m and _lib.STATIC_SCRATCH_BYTES == int(m.group(1)) * int(m.group(2)) * int(m.group(3))
+
+
+def test_one_launch_raster_support_and_argument_errors(L):
+    """beta_raster_fwd_bwd_l1 serves every tile shape with pixel-pair kernels
+    (not 8x4), and refuses bad arguments before anything is launched."""
+    for (tw, th), want in (((16, 16), 1), ((16, 8), 1), ((8, 8), 1), ((32, 16), 1), ((8, 4), 0), ((8, 16), 0)):
+        o = _lib.default_opts(tile_w=tw, tile_h=th)
+        assert L.beta_raster_fwd_bwd_l1_supported(ctypes.byref(o)) == want, (tw, th)
+    assert L.beta_raster_fwd_bwd_l1_supported(ctypes.byref(_lib.default_opts(alpha_max=1.0))) == 0
+    cams = _lib.make_cameras([scenes.pinhole(*scenes.look_at((0, 0, -3)), 64, 64)])
+    prm = _lib.make_params(10, 32, 1, 0x1000)
+    vp = ctypes.c_void_p(0x2000)
+    o = _lib.default_opts(tile_w=16, tile_h=8)
+
+    def call(opts, target=vp, grad2d=vp, ws=vp, ws_bytes=1 << 20):
+        return L.beta_raster_fwd_bwd_l1(ctypes.byref(prm), cams, 1, ctypes.byref(opts), vp, vp, vp, None, vp,
+                                        None, None, target, vp, None, grad2d, ws, ws_bytes, vp, None)
+
+    assert call(o, target=None) == _lib.BETA_ERR_ARG                         # no target
+    assert call(o, grad2d=ctypes.c_void_p(0x2004)) == _lib.BETA_ERR_ARG      # grad2d not 16-byte aligned
+    assert call(_lib.default_opts(tile_w=8, tile_h=4)) == _lib.BETA_ERR_ARG  # no pixel-pair kernels
+    assert call(o, ws=None) == _lib.BETA_ERR_WORKSPACE
+    assert call(o, ws_bytes=4) == _lib.BETA_ERR_WORKSPACE                    # one float per tile needed
